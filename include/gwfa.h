@@ -1,0 +1,204 @@
+/*
+ * gwfa.h -- C ABI of the GB300 graph wavefront alignment library (libgwfa.so).
+ *
+ * The library aligns DNA queries to a sequence graph G(V, E, sigma) (Def. 1 of
+ * "Fast sequence to graph alignment using the graph wavefront algorithm",
+ * Zhang, Wu, Aluru & Li): for a query q, a start vertex v_s and an end vertex
+ * v_e reachable from v_s, it returns the minimum edit distance between q and
+ * the spelled sequence of any walk from v_s to v_e, gaps at both ends penalised
+ * (Def. 2, the optimal global sequence-to-graph alignment).  The distance is
+ * computed by the graph wavefront algorithm (Alg. 1-3, Eq. 2) and optionally
+ * with the lag-based wavefront pruning heuristic (Alg. 4), whose distances are
+ * upper bounds.
+ *
+ * Conventions for every function:
+ *   - the return value is a status: GWFA_OK (0) or a negative GWFA_ERR_* code;
+ *     gwfa_strerror() gives its text;
+ *   - pointers named h_* / plain pointers are host memory, d_* are device
+ *     memory of the graph's GPU; the caller keeps ownership of every buffer it
+ *     passes and may free or reuse it when the call returns (for *_device calls:
+ *     once the work queued on `stream` has completed);
+ *   - a `stream` argument is a cudaStream_t passed as void*; NULL means the
+ *     library's own stream of that object;
+ *   - sequences are ASCII A/C/G/T, either case; anything else is rejected
+ *     (GWFA_ERR_INVALID) because sequences are stored 2-bit packed.
+ *   - all work runs in CUDA kernels on one GPU; there is no CPU fallback: if the
+ *     GPU or the kernels are unavailable the call fails with GWFA_ERR_CUDA.
+ */
+#ifndef GWFA_H
+#define GWFA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define GWFA_OK 0
+#define GWFA_PENDING 1              /* serving: request not finished yet */
+#define GWFA_ERR_INVALID (-1)       /* bad argument: non-ACGT base, empty label, id out of range */
+#define GWFA_ERR_OOM (-2)           /* device or host allocation failed */
+#define GWFA_ERR_CUDA (-3)          /* CUDA runtime error / no usable GPU */
+#define GWFA_ERR_UNREACHABLE (-4)   /* v_e is not reachable from v_s (Def. 2 requires it) */
+#define GWFA_ERR_EMPTY_FRONTIER (-5)/* pruning (Alg. 4) removed every live diagonal */
+#define GWFA_ERR_CAPACITY (-6)      /* per-query workspace too small (hash / frontier) */
+#define GWFA_ERR_TIMEOUT (-7)       /* a bounded device wait expired */
+#define GWFA_ERR_SCORE_LIMIT (-8)   /* distance exceeds opts.max_score */
+#define GWFA_ERR_NOT_RUN (-9)       /* query was not processed (batch aborted) */
+
+const char *gwfa_strerror(int status);
+
+/* ---- options and results ------------------------------------------------ */
+typedef struct {
+    int32_t max_lag;     /* a_diff of Alg. 4 (Sec. 2.5); 0 = exact (no pruning) */
+    int32_t traceback;   /* reserved, must be 0 */
+    int32_t max_score;   /* stop with GWFA_ERR_SCORE_LIMIT once d would exceed it; -1 = no limit */
+    int32_t wait_limit;  /* serving: iteration limit of device-side waits; 0 = default */
+} gwfa_opts;
+
+/*
+ * Per-query result.  Work counters follow Alg. 1-3 exactly and are identical
+ * for every execution order (the queue order of Alg. 2-3 does not change them):
+ *   n_scores      number of GwfExtend calls (= edit_distance + 1 on success);
+ *   cells         sum over scores of |Q| after GwfExtend (diagonals extended);
+ *   peak_frontier max over scores of |Q| after GwfExtend;
+ *   visited       distinct diagonals (v, k) ever inserted into H~;
+ *   pruned        diagonals dropped by GwfPrune, summed over scores;
+ *   spills        diagonals inserted by the arc loop of GwfExtend.
+ */
+typedef struct {
+    int32_t status;          /* GWFA_OK or GWFA_ERR_* */
+    int32_t edit_distance;   /* valid when status == GWFA_OK */
+    int32_t is_upper_bound;  /* 1 iff pruning dropped at least one diagonal */
+    uint32_t n_scores;
+    uint64_t cells;
+    uint64_t visited;
+    uint32_t peak_frontier;
+    uint32_t reserved;
+    uint64_t pruned;
+    uint64_t spills;
+} gwfa_result;               /* 56 bytes */
+
+/* ---- graph -------------------------------------------------------------- */
+typedef struct gwfa_graph gwfa_graph;
+
+/*
+ * Upload a sequence graph (Def. 1) to GPU `device` as 2-bit packed labels
+ * (16 bases per 32-bit word, each vertex starting on a word boundary) plus a
+ * CSR of out-arcs.
+ *   n_vertices       |V| (1 .. 2^31)
+ *   h_seq, h_seq_off labels concatenated: label v is h_seq[h_seq_off[v] .. h_seq_off[v+1]),
+ *                    h_seq_off has n_vertices+1 entries; every label must be non-empty
+ *                    (an empty label would create zero-cost cycles) and shorter than 2^30
+ *   n_arcs, h_arc_src, h_arc_dst   arcs (u, v) of E; duplicates are merged
+ * Errors: GWFA_ERR_INVALID (bad base, empty label, vertex id out of range),
+ * GWFA_ERR_OOM, GWFA_ERR_CUDA.  The graph is immutable afterwards and may be
+ * shared by any number of engines and threads.
+ */
+int gwfa_graph_create(uint32_t n_vertices, const char *h_seq, const uint64_t *h_seq_off,
+                      uint64_t n_arcs, const uint32_t *h_arc_src, const uint32_t *h_arc_dst,
+                      int device, gwfa_graph **out);
+int gwfa_graph_destroy(gwfa_graph *g);
+
+typedef struct {
+    uint32_t n_vertices;
+    uint32_t max_out_degree;
+    uint64_t n_arcs;          /* after merging duplicates */
+    uint64_t total_bases;
+    uint64_t device_bytes;    /* resident footprint of the packed graph */
+    int32_t device;
+    int32_t has_cycles;       /* 1 if some arc goes to an equal or lower vertex id */
+} gwfa_graph_info;
+int gwfa_graph_get_info(const gwfa_graph *g, gwfa_graph_info *out);
+
+/* ---- plain path: one query, one kernel launch, synchronous -------------- */
+/*
+ * Align one query (Alg. 1 with Alg. 2-4) with a single-CTA launch of the same
+ * kernel the batched path uses.  Host reachability check first
+ * (GWFA_ERR_UNREACHABLE).  Result in *out (host).  Uses a workspace owned by
+ * the graph, so concurrent gwfa_align calls on one graph are serialised.
+ */
+int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t v_s, uint32_t v_e,
+               const gwfa_opts *opts, gwfa_result *out);
+
+/* ---- batched path: persistent kernel with a device work queue ----------- */
+typedef struct gwfa_engine gwfa_engine;
+
+/*
+ * Engine = device workspace for batched alignment.  Each CTA of the persistent
+ * kernel owns one slab (per-query hash of diagonal tiles + frontier lists) and
+ * pulls query ids from an atomic queue; a query whose slab overflows is put on
+ * a retry list and re-run by the next tier (fewer CTAs, larger slabs) in the
+ * same stream, without a host round trip.
+ *   tiers[t].ctas  CTAs of tier t (0 = one per SM times the occupancy limit)
+ *   tiers[t].log2_tiles  slab capacity in 8-diagonal tiles (log2)
+ *   threads        threads per CTA (multiple of 32, 64..1024); 0 = 128
+ *   max_queries, max_bases  sizes of the engine's staging buffers for the
+ *                  host-buffer entry point (grown on demand)
+ */
+#define GWFA_MAX_TIERS 4
+typedef struct {
+    uint32_t ctas;
+    uint32_t log2_tiles;
+} gwfa_tier;
+
+typedef struct {
+    uint32_t n_tiers;
+    gwfa_tier tiers[GWFA_MAX_TIERS];
+    uint32_t threads;
+    uint32_t prune_slabs;     /* 1: size slabs for pruning mode (64-bit offsets) */
+    uint64_t max_queries;
+    uint64_t max_bases;
+} gwfa_engine_config;
+
+/* fills a default configuration for this GPU (3 tiers, 128 threads) */
+int gwfa_engine_default_config(const gwfa_graph *g, int prune, gwfa_engine_config *cfg);
+int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_engine **out);
+int gwfa_engine_destroy(gwfa_engine *e);
+/* bytes of device memory held by the engine */
+uint64_t gwfa_engine_device_bytes(const gwfa_engine *e);
+
+/*
+ * Host-buffer batch (end to end).  Queries concatenated in h_q (ASCII) with
+ * h_q_off[n_queries+1] byte offsets, per-query start/end vertices in
+ * h_v_s / h_v_e.  h_order (may be NULL = input order) is the order in which the
+ * work queue hands queries to CTAs (a permutation of 0..n_queries-1).  The call
+ * copies the inputs to the device, packs them (kernel), runs the tiers, copies
+ * the n_queries results to h_out and returns when they are there.  Per-query
+ * errors are in h_out[i].status; the return value is the first fatal error.
+ * For pinned host buffers the copies are asynchronous DMA.
+ */
+int gwfa_align_batch(gwfa_engine *e, uint32_t n_queries, const char *h_q, const uint64_t *h_q_off,
+                     const uint32_t *h_v_s, const uint32_t *h_v_e, const uint32_t *h_order,
+                     const gwfa_opts *opts, gwfa_result *h_out, void *stream);
+
+/*
+ * Device-resident packing of queries (the step gwfa_align_batch runs after its
+ * copy): d_q / d_q_off as above but in device memory; writes 2-bit words to
+ * d_words with query i starting at word (d_q_off[i] >> 4) + i, so d_words needs
+ * (q_off[n] >> 4) + n_queries + 2 words.  Queries with a non-ACGT base get
+ * status GWFA_ERR_INVALID in d_status (int32[n_queries]) and 0 otherwise.
+ */
+int gwfa_pack_queries_device(uint32_t n_queries, const char *d_q, const uint64_t *d_q_off,
+                             uint32_t *d_words, int32_t *d_status, void *stream);
+
+/*
+ * Device-resident batch (inputs already in HBM): d_words / d_q_off as written
+ * by gwfa_pack_queries_device (d_status may be NULL, else queries with a
+ * nonzero status are skipped and keep it), d_v_s / d_v_e start/end vertices,
+ * d_order the queue order (NULL = 0..n-1), results into d_out[n_queries].
+ * Asynchronous on `stream`; no host synchronisation inside.
+ */
+int gwfa_align_batch_device(gwfa_engine *e, uint32_t n_queries, const uint32_t *d_words,
+                            const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
+                            const uint32_t *d_order, const int32_t *d_status,
+                            const gwfa_opts *opts, gwfa_result *d_out, void *stream);
+
+/* number of kernel launches the last batch call on this engine queued */
+uint32_t gwfa_engine_last_launches(const gwfa_engine *e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWFA_H */

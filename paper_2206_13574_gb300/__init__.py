@@ -1,0 +1,292 @@
+"""Python binding of libgwfa.so (graph wavefront alignment on GB300).
+
+Argument marshalling only: every step of the alignment runs in the library's
+CUDA kernels.  Names follow the C ABI in include/gwfa.h.  PyTorch is used only
+to hold device buffers and to pass the current CUDA stream.  There is no CPU
+fallback: if libgwfa.so is missing or no GPU is usable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgwfa.so")
+
+GWFA_OK = 0
+GWFA_PENDING = 1
+GWFA_ERR_INVALID = -1
+GWFA_ERR_OOM = -2
+GWFA_ERR_CUDA = -3
+GWFA_ERR_UNREACHABLE = -4
+GWFA_ERR_EMPTY_FRONTIER = -5
+GWFA_ERR_CAPACITY = -6
+GWFA_ERR_TIMEOUT = -7
+GWFA_ERR_SCORE_LIMIT = -8
+GWFA_ERR_NOT_RUN = -9
+GWFA_MAX_TIERS = 4
+
+# numpy view of gwfa_result (56 bytes)
+RESULT_DTYPE = np.dtype([("status", "<i4"), ("edit_distance", "<i4"), ("is_upper_bound", "<i4"),
+                         ("n_scores", "<u4"), ("cells", "<u8"), ("visited", "<u8"),
+                         ("peak_frontier", "<u4"), ("reserved", "<u4"), ("pruned", "<u8"),
+                         ("spills", "<u8")])
+assert RESULT_DTYPE.itemsize == 56
+
+
+class gwfa_opts(ctypes.Structure):
+    _fields_ = [("max_lag", ctypes.c_int32), ("traceback", ctypes.c_int32),
+                ("max_score", ctypes.c_int32), ("wait_limit", ctypes.c_int32)]
+
+
+class gwfa_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("edit_distance", ctypes.c_int32),
+                ("is_upper_bound", ctypes.c_int32), ("n_scores", ctypes.c_uint32),
+                ("cells", ctypes.c_uint64), ("visited", ctypes.c_uint64),
+                ("peak_frontier", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("pruned", ctypes.c_uint64), ("spills", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class gwfa_graph_info(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_uint32), ("max_out_degree", ctypes.c_uint32),
+                ("n_arcs", ctypes.c_uint64), ("total_bases", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
+                ("has_cycles", ctypes.c_int32)]
+
+
+class gwfa_tier(ctypes.Structure):
+    _fields_ = [("ctas", ctypes.c_uint32), ("log2_tiles", ctypes.c_uint32)]
+
+
+class gwfa_engine_config(ctypes.Structure):
+    _fields_ = [("n_tiers", ctypes.c_uint32), ("tiers", gwfa_tier * GWFA_MAX_TIERS),
+                ("threads", ctypes.c_uint32), ("prune_slabs", ctypes.c_uint32),
+                ("max_queries", ctypes.c_uint64), ("max_bases", ctypes.c_uint64)]
+
+
+# every symbol include/gwfa.h declares, with its ctypes signature
+_P = ctypes.c_void_p
+_u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+SIGNATURES = {
+    "gwfa_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "gwfa_graph_create": ([_u32, _P, _P, _u64, _P, _P, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "gwfa_graph_destroy": ([_P], ctypes.c_int),
+    "gwfa_graph_get_info": ([_P, ctypes.POINTER(gwfa_graph_info)], ctypes.c_int),
+    "gwfa_align": ([_P, _P, _u32, _u32, _u32, ctypes.POINTER(gwfa_opts), ctypes.POINTER(gwfa_result)],
+                   ctypes.c_int),
+    "gwfa_engine_default_config": ([_P, ctypes.c_int, ctypes.POINTER(gwfa_engine_config)], ctypes.c_int),
+    "gwfa_engine_create": ([_P, ctypes.POINTER(gwfa_engine_config), ctypes.POINTER(_P)], ctypes.c_int),
+    "gwfa_engine_destroy": ([_P], ctypes.c_int),
+    "gwfa_engine_device_bytes": ([_P], _u64),
+    "gwfa_align_batch": ([_P, _u32, _P, _P, _P, _P, _P, ctypes.POINTER(gwfa_opts), _P, _P], ctypes.c_int),
+    "gwfa_pack_queries_device": ([_u32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "gwfa_align_batch_device": ([_P, _u32, _P, _P, _P, _P, _P, _P, ctypes.POINTER(gwfa_opts), _P, _P],
+                                ctypes.c_int),
+    "gwfa_engine_last_launches": ([_P], _u32),
+}
+
+_lib = None
+
+
+class GwfaError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})" if what else strerror(status))
+
+
+def load(path: str | None = None):
+    """Load libgwfa.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_2206_13574_gb300._build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    if _lib is None:
+        return f"status {status}"
+    return _lib.gwfa_strerror(status).decode()
+
+
+def _check(st: int, what: str):
+    if st != GWFA_OK:
+        raise GwfaError(st, what)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _opts(max_lag: int, max_score: int) -> gwfa_opts:
+    return gwfa_opts(int(max_lag), 0, int(max_score), 0)
+
+
+class Graph:
+    """A sequence graph resident on one GPU (gwfa_graph_create)."""
+
+    def __init__(self, seq, off, arc_src, arc_dst, device: int = 0):
+        lib = load()
+        self._seq = _c(seq, np.uint8)
+        self._off = _c(off, np.uint64)
+        src = _c(arc_src, np.uint32)
+        dst = _c(arc_dst, np.uint32)
+        h = _P()
+        _check(lib.gwfa_graph_create(len(self._off) - 1, self._seq.ctypes.data, self._off.ctypes.data,
+                                     len(src), src.ctypes.data, dst.ctypes.data, device,
+                                     ctypes.byref(h)), "gwfa_graph_create")
+        self.handle = h
+        self.device = device
+
+    @classmethod
+    def from_synth(cls, g, device: int = 0) -> "Graph":
+        return cls(g.seq, g.off, g.arc_src, g.arc_dst, device)
+
+    def info(self) -> dict:
+        i = gwfa_graph_info()
+        _check(load().gwfa_graph_get_info(self.handle, ctypes.byref(i)), "gwfa_graph_get_info")
+        return {k: int(getattr(i, k)) for k, _ in i._fields_}
+
+    def align(self, q: bytes, v_s: int, v_e: int, max_lag: int = 0, max_score: int = -1) -> dict:
+        """Plain path (gwfa_align): one query, one kernel launch, synchronous."""
+        r = gwfa_result()
+        o = _opts(max_lag, max_score)
+        qb = bytes(q)
+        _check(load().gwfa_align(self.handle, qb, len(qb), v_s, v_e, ctypes.byref(o), ctypes.byref(r)),
+               "gwfa_align")
+        return r.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gwfa_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_config(graph: Graph, prune: bool = False) -> gwfa_engine_config:
+    c = gwfa_engine_config()
+    _check(load().gwfa_engine_default_config(graph.handle, int(prune), ctypes.byref(c)),
+           "gwfa_engine_default_config")
+    return c
+
+
+class Engine:
+    """Batched alignment workspace (gwfa_engine_create)."""
+
+    def __init__(self, graph: Graph, prune: bool = False, config: gwfa_engine_config | None = None):
+        lib = load()
+        self.graph = graph
+        self.config = config if config is not None else default_config(graph, prune)
+        h = _P()
+        _check(lib.gwfa_engine_create(graph.handle, ctypes.byref(self.config), ctypes.byref(h)),
+               "gwfa_engine_create")
+        self.handle = h
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().gwfa_engine_device_bytes(self.handle))
+
+    @property
+    def last_launches(self) -> int:
+        return int(load().gwfa_engine_last_launches(self.handle))
+
+    def align_batch(self, seq, off, v_s, v_e, order=None, max_lag: int = 0, max_score: int = -1,
+                    stream: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        """Host buffers in, host results out (gwfa_align_batch)."""
+        seq = _c(seq, np.uint8)
+        off = _c(off, np.uint64)
+        vs = _c(v_s, np.uint32)
+        ve = _c(v_e, np.uint32)
+        n = len(vs)
+        res = out if out is not None else np.zeros(n, dtype=RESULT_DTYPE)
+        o = _opts(max_lag, max_score)
+        od = None if order is None else _c(order, np.uint32)
+        _check(load().gwfa_align_batch(self.handle, n, seq.ctypes.data, off.ctypes.data, vs.ctypes.data,
+                                       ve.ctypes.data, None if od is None else od.ctypes.data,
+                                       ctypes.byref(o), res.ctypes.data, stream or None),
+               "gwfa_align_batch")
+        return res
+
+    def align_batch_device(self, n: int, d_words: int, d_q_off: int, d_v_s: int, d_v_e: int,
+                           d_order: int | None, d_status: int | None, d_out: int,
+                           max_lag: int = 0, max_score: int = -1, stream: int = 0):
+        """Device pointers in and out, asynchronous on `stream` (gwfa_align_batch_device)."""
+        o = _opts(max_lag, max_score)
+        _check(load().gwfa_align_batch_device(self.handle, n, d_words, d_q_off, d_v_s, d_v_e,
+                                              d_order or None, d_status or None, ctypes.byref(o),
+                                              d_out, stream or None),
+               "gwfa_align_batch_device")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gwfa_engine_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_queries_device(n: int, d_q: int, d_q_off: int, d_words: int, d_status: int | None,
+                        stream: int = 0):
+    _check(load().gwfa_pack_queries_device(n, d_q, d_q_off, d_words, d_status or None, stream or None),
+           "gwfa_pack_queries_device")
+
+
+def words_needed(n_queries: int, n_bases: int) -> int:
+    """Words of the packed query buffer (query i starts at word (q_off[i] >> 4) + i)."""
+    return (n_bases >> 4) + n_queries + 2
+
+
+class DeviceBatch:
+    """A query batch resident in HBM as torch tensors: ASCII, offsets, packed words, ids."""
+
+    def __init__(self, queries, device: int = 0, order=None, stream=None):
+        import torch
+        dev = torch.device("cuda", device)
+        self.n = len(queries.v_s)
+        self.n_bases = int(queries.off[-1])
+        self.q = torch.from_numpy(_c(queries.seq, np.uint8)).to(dev)
+        self.q_off = torch.from_numpy(_c(queries.off, np.uint64).view(np.int64)).to(dev)
+        self.v_s = torch.from_numpy(_c(queries.v_s, np.uint32).view(np.int32)).to(dev)
+        self.v_e = torch.from_numpy(_c(queries.v_e, np.uint32).view(np.int32)).to(dev)
+        self.order = None if order is None else torch.from_numpy(
+            _c(order, np.uint32).view(np.int32)).to(dev)
+        self.words = torch.empty(words_needed(self.n, self.n_bases), dtype=torch.int32, device=dev)
+        self.status = torch.empty(self.n, dtype=torch.int32, device=dev)
+        self.out = torch.empty(self.n * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        pack_queries_device(self.n, self.q.data_ptr(), self.q_off.data_ptr(), self.words.data_ptr(),
+                            self.status.data_ptr(), st.cuda_stream)
+
+    def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.q.device)
+        engine.align_batch_device(self.n, self.words.data_ptr(), self.q_off.data_ptr(),
+                                  self.v_s.data_ptr(), self.v_e.data_ptr(),
+                                  None if self.order is None else self.order.data_ptr(),
+                                  self.status.data_ptr(), self.out.data_ptr(), max_lag, max_score,
+                                  st.cuda_stream)
+
+    def results(self) -> np.ndarray:
+        return self.out.cpu().numpy().view(RESULT_DTYPE)

@@ -1,0 +1,492 @@
+// gwfa_api.cu -- host side of the C ABI declared in include/gwfa.h.
+//
+// Graph upload (packing, arc merging, CSR), the plain one-query path, the
+// engine (per-CTA slabs in tiers, retry lists) and the batch entry points.
+// Every step of the alignment itself runs in the kernels of gwfa_kernels.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "gwfa_internal.cuh"
+
+using gwfa::TierArgs;
+
+namespace {
+
+int host_code(char c) {
+    switch (c) {
+    case 'A': case 'a': return 0;
+    case 'C': case 'c': return 1;
+    case 'G': case 'g': return 2;
+    case 'T': case 't': return 3;
+    default: return -1;
+    }
+}
+
+template <class T>
+int dmalloc(T **p, uint64_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc((void **)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return GWFA_ERR_OOM;
+    }
+    return GWFA_OK;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GWFA_OK;
+    if (e == cudaErrorMemoryAllocation) return GWFA_ERR_OOM;
+    return GWFA_ERR_CUDA;
+}
+
+// Grow-only device buffer.
+int ensure(uint8_t **buf, uint64_t *have, uint64_t need) {
+    if (*have >= need) return GWFA_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    uint64_t want = std::max<uint64_t>(need, 1 << 20);
+    if (dmalloc(buf, want)) return GWFA_ERR_OOM;
+    *have = want;
+    return GWFA_OK;
+}
+
+// Host reachability v_s -> v_e (Def. 2 assumes it; the paper's loop never ends otherwise).
+bool reachable(const gwfa_graph *g, uint32_t vs, uint32_t ve) {
+    if (vs == ve) return true;
+    std::vector<uint8_t> seen(g->nv, 0);
+    std::vector<uint32_t> st;
+    st.push_back(vs);
+    seen[vs] = 1;
+    while (!st.empty()) {
+        uint32_t v = st.back();
+        st.pop_back();
+        for (uint32_t a = g->h_arc_off[v]; a < g->h_arc_off[v + 1]; ++a) {
+            uint32_t u = g->h_arc_dst[a];
+            if (u == ve) return true;
+            if (!seen[u]) { seen[u] = 1; st.push_back(u); }
+        }
+    }
+    return false;
+}
+
+struct Carve {
+    uint8_t *base;
+    uint64_t off = 0;
+    template <class T> T *take(uint64_t bytes) {
+        T *p = (T *)(base + off);
+        off = gwfa::align256(off + bytes);
+        return p;
+    }
+};
+
+uint64_t words_for(uint32_t nq, uint64_t nbases) { return (nbases >> 4) + nq + 2; }
+
+}  // namespace
+
+extern "C" {
+
+const char *gwfa_strerror(int s) {
+    switch (s) {
+    case GWFA_OK: return "ok";
+    case GWFA_PENDING: return "pending";
+    case GWFA_ERR_INVALID: return "invalid argument";
+    case GWFA_ERR_OOM: return "out of memory";
+    case GWFA_ERR_CUDA: return "CUDA error";
+    case GWFA_ERR_UNREACHABLE: return "end vertex not reachable from start vertex";
+    case GWFA_ERR_EMPTY_FRONTIER: return "pruning emptied the wavefront";
+    case GWFA_ERR_CAPACITY: return "workspace capacity exceeded";
+    case GWFA_ERR_TIMEOUT: return "device wait timed out";
+    case GWFA_ERR_SCORE_LIMIT: return "edit distance above max_score";
+    case GWFA_ERR_NOT_RUN: return "query not run";
+    default: return "unknown status";
+    }
+}
+
+int gwfa_graph_create(uint32_t nv, const char *h_seq, const uint64_t *h_seq_off, uint64_t na,
+                      const uint32_t *h_arc_src, const uint32_t *h_arc_dst, int device,
+                      gwfa_graph **out) {
+    if (!out || !h_seq_off || (nv > 0 && !h_seq) || (na > 0 && (!h_arc_src || !h_arc_dst)))
+        return GWFA_ERR_INVALID;
+    *out = nullptr;
+    if (nv == 0 || nv >= 0x7FFFFFFFu) return GWFA_ERR_INVALID;
+    // labels: non-empty, ACGT, 2-bit packed, each vertex on a word boundary
+    std::vector<uint32_t> vstart(nv), vlen(nv);
+    uint64_t nwords = 0, total = 0;
+    for (uint32_t v = 0; v < nv; ++v) {
+        if (h_seq_off[v + 1] <= h_seq_off[v]) return GWFA_ERR_INVALID;
+        uint64_t L = h_seq_off[v + 1] - h_seq_off[v];
+        if (L >= (1ull << 30)) return GWFA_ERR_INVALID;
+        vlen[v] = (uint32_t)L;
+        vstart[v] = (uint32_t)nwords;
+        nwords += (L + 15) >> 4;
+        total += L;
+        if (nwords >= 0xFFFFFFF0ull) return GWFA_ERR_INVALID;
+    }
+    std::vector<uint32_t> words(nwords + 2, 0);
+    for (uint32_t v = 0; v < nv; ++v) {
+        const char *s = h_seq + h_seq_off[v];
+        uint32_t *w = words.data() + vstart[v];
+        for (uint32_t p = 0; p < vlen[v]; ++p) {
+            int c = host_code(s[p]);
+            if (c < 0) return GWFA_ERR_INVALID;
+            w[p >> 4] |= (uint32_t)c << (2 * (p & 15));
+        }
+    }
+    // arcs: validate, merge duplicates, CSR by source
+    std::vector<std::pair<uint32_t, uint32_t>> arcs(na);
+    int has_cycles = 0;
+    for (uint64_t a = 0; a < na; ++a) {
+        if (h_arc_src[a] >= nv || h_arc_dst[a] >= nv) return GWFA_ERR_INVALID;
+        arcs[a] = {h_arc_src[a], h_arc_dst[a]};
+        if (h_arc_dst[a] <= h_arc_src[a]) has_cycles = 1;
+    }
+    std::sort(arcs.begin(), arcs.end());
+    arcs.erase(std::unique(arcs.begin(), arcs.end()), arcs.end());
+    gwfa_graph *g = new (std::nothrow) gwfa_graph();
+    if (!g) return GWFA_ERR_OOM;
+    g->device = device;
+    g->nv = nv;
+    g->na = arcs.size();
+    g->total = total;
+    g->n_words = nwords + 2;
+    g->has_cycles = has_cycles;
+    g->h_arc_off.assign(nv + 1, 0);
+    g->h_arc_dst.resize(arcs.size());
+    for (auto &a : arcs) g->h_arc_off[a.first + 1]++;
+    for (uint32_t v = 0; v < nv; ++v) {
+        g->max_outdeg = std::max(g->max_outdeg, g->h_arc_off[v + 1]);
+        g->h_arc_off[v + 1] += g->h_arc_off[v];
+    }
+    for (size_t a = 0; a < arcs.size(); ++a) g->h_arc_dst[a] = arcs[a].second;
+
+    int st = cuda_status(cudaSetDevice(device));
+    if (st) { delete g; return st; }
+    st = dmalloc(&g->d_words, g->n_words * 4);
+    if (!st) st = dmalloc(&g->d_vstart, (uint64_t)nv * 4);
+    if (!st) st = dmalloc(&g->d_vlen, (uint64_t)nv * 4);
+    if (!st) st = dmalloc(&g->d_arc_off, (uint64_t)(nv + 1) * 4);
+    if (!st) st = dmalloc(&g->d_arc_dst, std::max<uint64_t>(g->na, 1) * 4);
+    if (!st) st = cuda_status(cudaMemcpy(g->d_words, words.data(), g->n_words * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cuda_status(cudaMemcpy(g->d_vstart, vstart.data(), (uint64_t)nv * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cuda_status(cudaMemcpy(g->d_vlen, vlen.data(), (uint64_t)nv * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cuda_status(cudaMemcpy(g->d_arc_off, g->h_arc_off.data(), (uint64_t)(nv + 1) * 4, cudaMemcpyHostToDevice));
+    if (!st && g->na) st = cuda_status(cudaMemcpy(g->d_arc_dst, g->h_arc_dst.data(), g->na * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cuda_status(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    g->device_bytes = g->n_words * 4 + (uint64_t)nv * 8 + (uint64_t)(nv + 1) * 4 + g->na * 4;
+    if (st) { gwfa_graph_destroy(g); return st; }
+    *out = g;
+    return GWFA_OK;
+}
+
+int gwfa_graph_destroy(gwfa_graph *g) {
+    if (!g) return GWFA_ERR_INVALID;
+    cudaSetDevice(g->device);
+    cudaFree(g->d_words);
+    cudaFree(g->d_vstart);
+    cudaFree(g->d_vlen);
+    cudaFree(g->d_arc_off);
+    cudaFree(g->d_arc_dst);
+    cudaFree(g->plain_slab);
+    cudaFree(g->plain_stage);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+    return GWFA_OK;
+}
+
+int gwfa_graph_get_info(const gwfa_graph *g, gwfa_graph_info *o) {
+    if (!g || !o) return GWFA_ERR_INVALID;
+    o->n_vertices = g->nv;
+    o->max_out_degree = g->max_outdeg;
+    o->n_arcs = g->na;
+    o->total_bases = g->total;
+    o->device_bytes = g->device_bytes;
+    o->device = g->device;
+    o->has_cycles = g->has_cycles;
+    return GWFA_OK;
+}
+
+// ---------------------------------------------------------------- plain path
+
+int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
+               const gwfa_opts *opts, gwfa_result *out) {
+    if (!g || !out || (n > 0 && !h_q)) return GWFA_ERR_INVALID;
+    gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
+    memset(out, 0, sizeof(*out));
+    out->edit_distance = -1;
+    if (vs >= g->nv || ve >= g->nv || o.max_lag < 0 || o.traceback != 0 || n >= 0x7FFFFFFFu) {
+        out->status = GWFA_ERR_INVALID;
+        return GWFA_ERR_INVALID;
+    }
+    if (!reachable(g, vs, ve)) {
+        out->status = GWFA_ERR_UNREACHABLE;
+        return GWFA_OK;
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    int st = cuda_status(cudaSetDevice(g->device));
+    if (st) return st;
+    const bool prune = o.max_lag > 0;
+    // staging: query bytes | q_off[2] | v_s | v_e | words | status | head | result
+    const uint64_t need = gwfa::align256(n + 16) + 256 * 5 + gwfa::align256(words_for(1, n) * 4) +
+                          gwfa::align256(sizeof(gwfa_result)) + 1024;
+    st = ensure(&g->plain_stage, &g->plain_stage_bytes, need);
+    if (st) return st;
+    Carve c{g->plain_stage};
+    char *d_q = c.take<char>(n + 16);
+    uint64_t *d_off = c.take<uint64_t>(16);
+    uint32_t *d_vs = c.take<uint32_t>(4);
+    uint32_t *d_ve = c.take<uint32_t>(4);
+    int32_t *d_status = c.take<int32_t>(4);
+    uint32_t *d_head = c.take<uint32_t>(4);
+    gwfa_result *d_res = c.take<gwfa_result>(sizeof(gwfa_result));
+    uint32_t *d_words = c.take<uint32_t>(words_for(1, n) * 4);
+    uint64_t h_off[2] = {0, n};
+    cudaStream_t s = g->stream;
+    uint32_t log2 = g->plain_log2 && g->plain_prune == prune ? g->plain_log2 : (prune ? 15u : 16u);
+    for (;;) {
+        if (!g->plain_slab || g->plain_log2 != log2 || g->plain_prune != prune) {
+            cudaFree(g->plain_slab);
+            g->plain_slab = nullptr;
+            const uint64_t bytes = gwfa::slab_layout(log2, prune).total;
+            st = dmalloc(&g->plain_slab, bytes);
+            if (st) return st;
+            st = cuda_status(gwfa::launch_fill(g->plain_slab, bytes, s));
+            if (st) return st;
+            g->plain_log2 = log2;
+            g->plain_prune = prune;
+        }
+        if (n) cudaMemcpyAsync(d_q, h_q, n, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_off, h_off, 16, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_vs, &vs, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_ve, &ve, 4, cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(d_head, 0, 4, s);
+        st = cuda_status(gwfa::launch_pack(1, d_q, d_off, d_words, d_status, s));
+        if (st) return st;
+        TierArgs a{};
+        a.g = g->dev();
+        a.qwords = d_words;
+        a.q_off = d_off;
+        a.v_s = d_vs;
+        a.v_e = d_ve;
+        a.qstatus = d_status;
+        a.out = d_res;
+        a.list = nullptr;
+        a.list_count = nullptr;
+        a.count_val = 1;
+        a.retry = nullptr;
+        a.retry_count = nullptr;
+        a.head = d_head;
+        a.slabs = g->plain_slab;
+        a.slab_bytes = gwfa::slab_layout(log2, prune).total;
+        a.log2cap = log2;
+        a.max_lag = o.max_lag;
+        a.max_score = o.max_score;
+        st = cuda_status(gwfa::launch_align(a, prune, 1, 128, s));
+        if (st) return st;
+        st = cuda_status(cudaMemcpyAsync(out, d_res, sizeof(gwfa_result), cudaMemcpyDeviceToHost, s));
+        if (!st) st = cuda_status(cudaStreamSynchronize(s));
+        if (st) return st;
+        if (out->status == GWFA_ERR_CAPACITY && log2 < 24) {
+            log2 += 3;   // grow the workspace and run again
+            continue;
+        }
+        return GWFA_OK;
+    }
+}
+
+// ---------------------------------------------------------------- engine
+
+int gwfa_engine_default_config(const gwfa_graph *g, int prune, gwfa_engine_config *cfg) {
+    if (!g || !cfg) return GWFA_ERR_INVALID;
+    memset(cfg, 0, sizeof(*cfg));
+    int st = cuda_status(cudaSetDevice(g->device));
+    if (st) return st;
+    int sms = 0, bps = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+        return GWFA_ERR_CUDA;
+    cfg->threads = 128;
+    if (gwfa::align_occupancy(prune != 0, cfg->threads, &bps) || bps < 1) bps = 1;
+    cfg->n_tiers = 3;
+    cfg->tiers[0] = {(uint32_t)(sms * bps), prune ? 15u : 16u};
+    cfg->tiers[1] = {(uint32_t)sms, 19u};
+    cfg->tiers[2] = {(uint32_t)std::max(sms / 16, 1), 22u};
+    cfg->prune_slabs = prune ? 1 : 0;
+    cfg->max_queries = 1 << 16;
+    cfg->max_bases = 1ull << 28;
+    return GWFA_OK;
+}
+
+int gwfa_engine_destroy(gwfa_engine *e) {
+    if (!e) return GWFA_ERR_INVALID;
+    cudaSetDevice(e->g->device);
+    for (int t = 0; t < GWFA_MAX_TIERS; ++t) cudaFree(e->slabs[t]);
+    cudaFree(e->counters);
+    cudaFree(e->retry_lists);
+    cudaFree(e->stage);
+    if (e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+    return GWFA_OK;
+}
+
+static int engine_retry_capacity(gwfa_engine *e, uint64_t n) {
+    if (e->retry_cap >= n) return GWFA_OK;
+    cudaFree(e->retry_lists);
+    e->retry_lists = nullptr;
+    e->retry_cap = 0;
+    uint64_t want = std::max<uint64_t>(n, 1024);
+    if (dmalloc(&e->retry_lists, want * 4 * GWFA_MAX_TIERS)) return GWFA_ERR_OOM;
+    e->retry_cap = want;
+    return GWFA_OK;
+}
+
+int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_engine **out) {
+    if (!g || !cfg || !out) return GWFA_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->n_tiers < 1 || cfg->n_tiers > GWFA_MAX_TIERS) return GWFA_ERR_INVALID;
+    const uint32_t threads = cfg->threads ? cfg->threads : 128;
+    if (threads % 32 || threads < 64 || threads > 512) return GWFA_ERR_INVALID;
+    for (uint32_t t = 0; t < cfg->n_tiers; ++t)
+        if (cfg->tiers[t].ctas == 0 || cfg->tiers[t].log2_tiles < 8 || cfg->tiers[t].log2_tiles > 28)
+            return GWFA_ERR_INVALID;
+    int st = cuda_status(cudaSetDevice(g->device));
+    if (st) return st;
+    gwfa_engine *e = new (std::nothrow) gwfa_engine();
+    if (!e) return GWFA_ERR_OOM;
+    e->g = g;
+    e->cfg = *cfg;
+    e->cfg.threads = threads;
+    st = cuda_status(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    for (uint32_t t = 0; !st && t < cfg->n_tiers; ++t) {
+        e->slab_bytes[t] = gwfa::slab_layout(cfg->tiers[t].log2_tiles, cfg->prune_slabs != 0).total;
+        const uint64_t bytes = e->slab_bytes[t] * cfg->tiers[t].ctas;
+        st = dmalloc(&e->slabs[t], bytes);
+        if (!st) st = cuda_status(gwfa::launch_fill(e->slabs[t], bytes, e->stream));
+        e->device_bytes += bytes;
+    }
+    if (!st) st = dmalloc(&e->counters, 256);
+    if (!st) st = engine_retry_capacity(e, cfg->max_queries);
+    if (!st) st = cuda_status(cudaStreamSynchronize(e->stream));
+    if (st) { gwfa_engine_destroy(e); return st; }
+    *out = e;
+    return GWFA_OK;
+}
+
+uint64_t gwfa_engine_device_bytes(const gwfa_engine *e) {
+    return e ? e->device_bytes + e->retry_cap * 4 * GWFA_MAX_TIERS + e->stage_bytes : 0;
+}
+
+uint32_t gwfa_engine_last_launches(const gwfa_engine *e) { return e ? e->last_launches : 0; }
+
+int gwfa_pack_queries_device(uint32_t n_queries, const char *d_q, const uint64_t *d_q_off,
+                             uint32_t *d_words, int32_t *d_status, void *stream) {
+    if (!d_q_off || !d_words || (n_queries && !d_q)) return GWFA_ERR_INVALID;
+    return cuda_status(gwfa::launch_pack(n_queries, d_q, d_q_off, d_words, d_status,
+                                         (cudaStream_t)stream));
+}
+
+static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const uint64_t *d_q_off,
+                     const uint32_t *d_vs, const uint32_t *d_ve, const uint32_t *d_order,
+                     const int32_t *d_status, const gwfa_opts &o, gwfa_result *d_out,
+                     cudaStream_t s) {
+    int st = engine_retry_capacity(e, n);
+    if (st) return st;
+    const uint32_t T = e->cfg.n_tiers;
+    uint32_t *heads = e->counters, *rcount = e->counters + GWFA_MAX_TIERS;
+    st = cuda_status(cudaMemsetAsync(e->counters, 0, 256, s));
+    if (st) return st;
+    const bool prune = o.max_lag > 0;
+    e->last_launches = 0;
+    for (uint32_t t = 0; t < T; ++t) {
+        TierArgs a{};
+        a.g = e->g->dev();
+        a.qwords = d_words;
+        a.q_off = d_q_off;
+        a.v_s = d_vs;
+        a.v_e = d_ve;
+        a.qstatus = d_status;
+        a.out = d_out;
+        a.list = t == 0 ? d_order : e->retry_lists + (uint64_t)(t - 1) * e->retry_cap;
+        a.list_count = t == 0 ? nullptr : rcount + (t - 1);
+        a.count_val = n;
+        a.retry = t + 1 < T ? e->retry_lists + (uint64_t)t * e->retry_cap : nullptr;
+        a.retry_count = rcount + t;
+        a.head = heads + t;
+        a.slabs = e->slabs[t];
+        a.slab_bytes = e->slab_bytes[t];
+        a.log2cap = e->cfg.tiers[t].log2_tiles;
+        a.max_lag = o.max_lag;
+        a.max_score = o.max_score;
+        st = cuda_status(gwfa::launch_align(a, prune, e->cfg.tiers[t].ctas, e->cfg.threads, s));
+        if (st) return st;
+        e->last_launches++;
+    }
+    return GWFA_OK;
+}
+
+int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
+                            const uint64_t *d_q_off, const uint32_t *d_vs, const uint32_t *d_ve,
+                            const uint32_t *d_order, const int32_t *d_status,
+                            const gwfa_opts *opts, gwfa_result *d_out, void *stream) {
+    if (!e || !d_words || !d_q_off || !d_vs || !d_ve || !d_out) return GWFA_ERR_INVALID;
+    gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
+    if (o.max_lag < 0 || o.traceback != 0) return GWFA_ERR_INVALID;
+    if (o.max_lag > 0 && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
+    if (n == 0) return GWFA_OK;
+    std::lock_guard<std::mutex> lk(e->mu);
+    int st = cuda_status(cudaSetDevice(e->g->device));
+    if (st) return st;
+    cudaStream_t s = stream ? (cudaStream_t)stream : e->stream;
+    return run_tiers(e, n, d_words, d_q_off, d_vs, d_ve, d_order, d_status, o, d_out, s);
+}
+
+int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t *h_q_off,
+                     const uint32_t *h_vs, const uint32_t *h_ve, const uint32_t *h_order,
+                     const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
+    if (!e || !h_q_off || !h_vs || !h_ve || !h_out) return GWFA_ERR_INVALID;
+    gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
+    if (o.max_lag < 0 || o.traceback != 0) return GWFA_ERR_INVALID;
+    if (o.max_lag > 0 && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
+    if (n == 0) return GWFA_OK;
+    if (h_q_off[0] != 0) return GWFA_ERR_INVALID;
+    const uint64_t nb = h_q_off[n];
+    if (nb > 0 && !h_q) return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(e->mu);
+    int st = cuda_status(cudaSetDevice(e->g->device));
+    if (st) return st;
+    cudaStream_t s = stream ? (cudaStream_t)stream : e->stream;
+    const uint64_t need = gwfa::align256(nb + 16) + gwfa::align256((uint64_t)(n + 1) * 8) +
+                          3 * gwfa::align256((uint64_t)n * 4) + gwfa::align256((uint64_t)n * 4) +
+                          gwfa::align256(words_for(n, nb) * 4) +
+                          gwfa::align256((uint64_t)n * sizeof(gwfa_result)) + 4096;
+    st = ensure(&e->stage, &e->stage_bytes, need);
+    if (st) return st;
+    Carve c{e->stage};
+    char *d_q = c.take<char>(nb + 16);
+    uint64_t *d_off = c.take<uint64_t>((uint64_t)(n + 1) * 8);
+    uint32_t *d_vs = c.take<uint32_t>((uint64_t)n * 4);
+    uint32_t *d_ve = c.take<uint32_t>((uint64_t)n * 4);
+    uint32_t *d_order = c.take<uint32_t>((uint64_t)n * 4);
+    int32_t *d_status = c.take<int32_t>((uint64_t)n * 4);
+    uint32_t *d_words = c.take<uint32_t>(words_for(n, nb) * 4);
+    gwfa_result *d_out = c.take<gwfa_result>((uint64_t)n * sizeof(gwfa_result));
+    st = cuda_status(cudaMemcpyAsync(d_q, h_q, nb, cudaMemcpyHostToDevice, s));
+    if (!st) st = cuda_status(cudaMemcpyAsync(d_off, h_q_off, (uint64_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (!st) st = cuda_status(cudaMemcpyAsync(d_vs, h_vs, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
+    if (!st) st = cuda_status(cudaMemcpyAsync(d_ve, h_ve, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
+    if (!st && h_order) st = cuda_status(cudaMemcpyAsync(d_order, h_order, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
+    if (!st) st = cuda_status(gwfa::launch_pack(n, d_q, d_off, d_words, d_status, s));
+    if (!st) st = run_tiers(e, n, d_words, d_off, d_vs, d_ve, h_order ? d_order : nullptr, d_status, o, d_out, s);
+    if (!st) e->last_launches += 1;
+    if (!st) st = cuda_status(cudaMemcpyAsync(h_out, d_out, (uint64_t)n * sizeof(gwfa_result), cudaMemcpyDeviceToHost, s));
+    if (!st) st = cuda_status(cudaStreamSynchronize(s));
+    return st;
+}
+
+}  // extern "C"

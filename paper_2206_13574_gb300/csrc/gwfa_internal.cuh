@@ -1,0 +1,128 @@
+// gwfa_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/gwfa.h"
+
+namespace gwfa {
+
+// A tile groups the 8 diagonals k = 8*kb .. 8*kb+7 of one vertex: its 8 offsets
+// H~_{v,k} are one 32-byte sector (exact mode) and are processed by 8 adjacent
+// lanes of a warp, so that the expand step (Alg. 3) is a shuffle inside the tile.
+constexpr int kTile = 8;
+constexpr uint64_t kEmptyKey = ~0ull;
+
+// Packed graph resident on the device (a1): labels 2-bit packed, base t of a word
+// in bits 2t..2t+1, every vertex starting on a word boundary, 2 zero pad words at
+// the end so that a 32-base window may always read two consecutive words.
+struct DevGraph {
+    const uint32_t *words;
+    const uint32_t *vstart;   // word index of each label
+    const uint32_t *vlen;     // |v|
+    const uint32_t *arc_off;  // CSR of out-arcs, nv + 1
+    const uint32_t *arc_dst;
+    uint32_t nv;
+};
+
+// Per-CTA slab layout (all arrays 256-byte aligned), cap = 2^log2 tiles.
+struct SlabLayout {
+    uint64_t keys, reg0, reg1, vals, touched, qlist, slist0, slist1, eslot, emask, evals, req, total;
+};
+
+__host__ __device__ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+__host__ __device__ inline SlabLayout slab_layout(uint32_t log2cap, bool prune) {
+    const uint64_t cap = 1ull << log2cap;
+    const uint64_t vb = prune ? 8 : 4;
+    SlabLayout L;
+    uint64_t o = 0;
+    L.keys = o;    o = align256(o + cap * 8);
+    L.reg0 = o;    o = align256(o + cap * 8);
+    L.reg1 = o;    o = align256(o + cap * 8);
+    L.vals = o;    o = align256(o + cap * kTile * vb);
+    L.touched = o; o = align256(o + cap * 4);
+    L.qlist = o;   o = align256(o + cap * 4);
+    L.slist0 = o;  o = align256(o + cap * 4);
+    L.slist1 = o;  o = align256(o + cap * 4);
+    L.eslot = o;   o = align256(o + cap * 4);
+    L.emask = o;   o = align256(o + cap * 4);
+    L.evals = o;   o = align256(o + cap * kTile * vb);
+    L.req = o;     o = align256(o + (prune ? cap * 16 : 0));
+    L.total = o;
+    return L;
+}
+
+// Arguments of one tier launch of the alignment kernel.
+struct TierArgs {
+    DevGraph g;
+    const uint32_t *qwords;     // packed queries; query i starts at word (q_off[i] >> 4) + i
+    const uint64_t *q_off;      // byte offsets of the ASCII queries, n + 1
+    const uint32_t *v_s, *v_e;
+    const int32_t *qstatus;     // optional pre-status (pack errors)
+    gwfa_result *out;
+    const uint32_t *list;       // query ids to run (NULL: identity)
+    const uint32_t *list_count; // device count (NULL: use count_val)
+    uint32_t count_val;
+    uint32_t *retry;            // overflowing query ids for the next tier (NULL: last tier)
+    uint32_t *retry_count;
+    uint32_t *head;             // work-queue head
+    uint8_t *slabs;
+    uint64_t slab_bytes;
+    uint32_t log2cap;
+    int32_t max_lag;
+    int32_t max_score;
+};
+
+// launchers (gwfa_kernels.cu)
+cudaError_t launch_align(const TierArgs &a, bool prune, uint32_t ctas, uint32_t threads,
+                         cudaStream_t st);
+cudaError_t launch_pack(uint32_t nq, const char *d_q, const uint64_t *d_off, uint32_t *d_words,
+                        int32_t *d_status, cudaStream_t st);
+cudaError_t launch_fill(void *p, uint64_t bytes, cudaStream_t st);
+int align_occupancy(bool prune, uint32_t threads, int *blocks_per_sm);
+
+}  // namespace gwfa
+
+struct gwfa_graph {
+    int device = 0;
+    uint32_t nv = 0;
+    uint64_t na = 0, total = 0, n_words = 0;
+    uint32_t max_outdeg = 0;
+    int has_cycles = 0;
+    std::vector<uint32_t> h_arc_off, h_arc_dst;
+    uint32_t *d_words = nullptr, *d_vstart = nullptr, *d_vlen = nullptr, *d_arc_off = nullptr,
+             *d_arc_dst = nullptr;
+    uint64_t device_bytes = 0;
+    // plain-path workspace (one slab), guarded by mu
+    mutable std::mutex mu;
+    mutable uint8_t *plain_slab = nullptr;
+    mutable uint32_t plain_log2 = 0;
+    mutable bool plain_prune = false;
+    mutable uint8_t *plain_stage = nullptr;   // query bytes + words + counters + result
+    mutable uint64_t plain_stage_bytes = 0;
+    mutable cudaStream_t stream = nullptr;
+    gwfa::DevGraph dev() const {
+        return gwfa::DevGraph{d_words, d_vstart, d_vlen, d_arc_off, d_arc_dst, nv};
+    }
+};
+
+struct gwfa_engine {
+    const gwfa_graph *g = nullptr;
+    gwfa_engine_config cfg{};
+    uint8_t *slabs[GWFA_MAX_TIERS] = {};
+    uint64_t slab_bytes[GWFA_MAX_TIERS] = {};
+    uint32_t *counters = nullptr;   // per tier: head, retry_count; plus retry lists
+    uint32_t *retry_lists = nullptr;
+    uint64_t retry_cap = 0;
+    // staging for the host-buffer entry point
+    uint8_t *stage = nullptr;
+    uint64_t stage_bytes = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t device_bytes = 0;
+    uint32_t last_launches = 0;
+    std::mutex mu;
+};
