@@ -136,6 +136,7 @@ def main():
     ap.add_argument("--queries", type=int, default=None, help="override the batch size")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-wide", type=int, default=0, help="queries on the wide CTA class")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -177,8 +178,9 @@ def main():
 
     graph = gw.Graph.from_synth(g, device=local)
     eng = gw.Engine(graph)
-    # longest queries first (a plain length-sorted schedule)
+    # longest queries first (a plain length-sorted schedule); the longest go to wide CTAs
     order = np.argsort(-qs.lengths(), kind="stable").astype(np.uint32)
+    n_wide = max(args.n_wide, 0) if eng.config.wide.ctas else 0
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         batch = gw.DeviceBatch(qs, device=local, order=order, stream=stream)
@@ -186,7 +188,7 @@ def main():
     torch.cuda.synchronize()
 
     def step():
-        batch.run(eng, stream=stream)
+        batch.run(eng, stream=stream, n_wide=n_wide)
 
     for _ in range(args.warmup):
         step()
@@ -237,7 +239,7 @@ def main():
 
     def e2e_step():
         st = lib.gwfa_align_batch(eng.handle, len(qs), h_q.data_ptr(), h_off.data_ptr(), h_vs.data_ptr(),
-                                  h_ve.data_ptr(), h_order.data_ptr(), ctypes.byref(opts),
+                                  h_ve.data_ptr(), h_order.data_ptr(), n_wide, ctypes.byref(opts),
                                   h_out.data_ptr(), stream.cuda_stream)
         assert st == 0, st
 
@@ -280,8 +282,11 @@ def main():
                        "aligned_bases": aligned_bp, "cells": cells,
                        "parallelism": f"query-sharded x{ws} (replicated graph)",
                        "l2": "flushed (256 MB write) before every timed step",
-                       "schedule": "longest query first", "engine_tiers": [
-                           [eng.config.tiers[t].ctas, eng.config.tiers[t].log2_tiles]
+                       "schedule": "longest query first", "n_wide": n_wide,
+                       "wide": [eng.config.wide.ctas, eng.config.wide.log2_tiles, eng.config.wide.threads],
+                       "engine_tiers": [
+                           [eng.config.tiers[t].ctas, eng.config.tiers[t].log2_tiles,
+                            eng.config.tiers[t].threads or eng.config.threads]
                            for t in range(eng.config.n_tiers)],
                        "threads_per_cta": eng.config.threads,
                        "ok_queries": int(ok.sum())},

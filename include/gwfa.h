@@ -75,7 +75,7 @@ typedef struct {
     uint64_t cells;
     uint64_t visited;
     uint32_t peak_frontier;
-    uint32_t reserved;
+    uint32_t device_us;      /* device time the CTA spent on this query, microseconds */
     uint64_t pruned;
     uint64_t spills;
 } gwfa_result;               /* 56 bytes */
@@ -131,9 +131,13 @@ typedef struct gwfa_engine gwfa_engine;
  * pulls query ids from an atomic queue; a query whose slab overflows is put on
  * a retry list and re-run by the next tier (fewer CTAs, larger slabs) in the
  * same stream, without a host round trip.
- *   tiers[t].ctas  CTAs of tier t (0 = one per SM times the occupancy limit)
+ *   tiers[t].ctas  CTAs of tier t
  *   tiers[t].log2_tiles  slab capacity in 8-diagonal tiles (log2)
- *   threads        threads per CTA (multiple of 32, 64..1024); 0 = 128
+ *   tiers[t].threads     threads per CTA of tier t (0 = `threads`)
+ *   wide           an extra set of (typically 512-thread) CTAs that runs concurrently
+ *                  with tier 0 on the first n_wide queries of the schedule, so that
+ *                  the heaviest queries do not form a tail behind narrow CTAs
+ *   threads        threads per CTA (multiple of 32, 64..512); 0 = 128
  *   max_queries, max_bases  sizes of the engine's staging buffers for the
  *                  host-buffer entry point (grown on demand)
  */
@@ -141,11 +145,14 @@ typedef struct gwfa_engine gwfa_engine;
 typedef struct {
     uint32_t ctas;
     uint32_t log2_tiles;
+    uint32_t threads;         /* threads per CTA of this tier; 0 = the config's `threads` */
+    uint32_t reserved;
 } gwfa_tier;
 
 typedef struct {
     uint32_t n_tiers;
     gwfa_tier tiers[GWFA_MAX_TIERS];
+    gwfa_tier wide;           /* CTAs for the heaviest queries, run beside tier 0; ctas 0 = none */
     uint32_t threads;
     uint32_t prune_slabs;     /* 1: size slabs for pruning mode (64-bit offsets) */
     uint64_t max_queries;
@@ -163,7 +170,8 @@ uint64_t gwfa_engine_device_bytes(const gwfa_engine *e);
  * Host-buffer batch (end to end).  Queries concatenated in h_q (ASCII) with
  * h_q_off[n_queries+1] byte offsets, per-query start/end vertices in
  * h_v_s / h_v_e.  h_order (may be NULL = input order) is the order in which the
- * work queue hands queries to CTAs (a permutation of 0..n_queries-1).  The call
+ * work queue hands queries to CTAs (a permutation of 0..n_queries-1); its first
+ * n_wide entries go to the engine's wide CTAs (0 = none).  The call
  * copies the inputs to the device, packs them (kernel), runs the tiers, copies
  * the n_queries results to h_out and returns when they are there.  Per-query
  * errors are in h_out[i].status; the return value is the first fatal error.
@@ -171,7 +179,7 @@ uint64_t gwfa_engine_device_bytes(const gwfa_engine *e);
  */
 int gwfa_align_batch(gwfa_engine *e, uint32_t n_queries, const char *h_q, const uint64_t *h_q_off,
                      const uint32_t *h_v_s, const uint32_t *h_v_e, const uint32_t *h_order,
-                     const gwfa_opts *opts, gwfa_result *h_out, void *stream);
+                     uint32_t n_wide, const gwfa_opts *opts, gwfa_result *h_out, void *stream);
 
 /*
  * Device-resident packing of queries (the step gwfa_align_batch runs after its
@@ -187,16 +195,28 @@ int gwfa_pack_queries_device(uint32_t n_queries, const char *d_q, const uint64_t
  * Device-resident batch (inputs already in HBM): d_words / d_q_off as written
  * by gwfa_pack_queries_device (d_status may be NULL, else queries with a
  * nonzero status are skipped and keep it), d_v_s / d_v_e start/end vertices,
- * d_order the queue order (NULL = 0..n-1), results into d_out[n_queries].
+ * d_order the queue order (NULL = 0..n-1) whose first n_wide entries go to the
+ * wide CTAs, results into d_out[n_queries].
  * Asynchronous on `stream`; no host synchronisation inside.
  */
 int gwfa_align_batch_device(gwfa_engine *e, uint32_t n_queries, const uint32_t *d_words,
                             const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
-                            const uint32_t *d_order, const int32_t *d_status,
+                            const uint32_t *d_order, uint32_t n_wide, const int32_t *d_status,
                             const gwfa_opts *opts, gwfa_result *d_out, void *stream);
 
 /* number of kernel launches the last batch call on this engine queued */
 uint32_t gwfa_engine_last_launches(const gwfa_engine *e);
+
+/*
+ * Per-query statistics of later batch calls on this engine (NULL = off): the
+ * kernels write 8 uint64 per query id into d_stats (device memory of
+ * n_queries * 8 words, owned by the caller, valid until replaced): time spent in
+ * GwfExtend and in GwfExpand (ns, measured by the CTA), extension rounds,
+ * tiles extended, tiles expanded, largest expanded-tile count of a score, tiles
+ * claimed in the hash, and the number of scores.  These are the wavefront sizes
+ * the learned cost model trains on.
+ */
+int gwfa_engine_set_stats(gwfa_engine *e, uint64_t *d_stats);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ GWFA_MAX_TIERS = 4
 # numpy view of gwfa_result (56 bytes)
 RESULT_DTYPE = np.dtype([("status", "<i4"), ("edit_distance", "<i4"), ("is_upper_bound", "<i4"),
                          ("n_scores", "<u4"), ("cells", "<u8"), ("visited", "<u8"),
-                         ("peak_frontier", "<u4"), ("reserved", "<u4"), ("pruned", "<u8"),
+                         ("peak_frontier", "<u4"), ("device_us", "<u4"), ("pruned", "<u8"),
                          ("spills", "<u8")])
 assert RESULT_DTYPE.itemsize == 56
 
@@ -45,11 +45,11 @@ class gwfa_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("edit_distance", ctypes.c_int32),
                 ("is_upper_bound", ctypes.c_int32), ("n_scores", ctypes.c_uint32),
                 ("cells", ctypes.c_uint64), ("visited", ctypes.c_uint64),
-                ("peak_frontier", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("peak_frontier", ctypes.c_uint32), ("device_us", ctypes.c_uint32),
                 ("pruned", ctypes.c_uint64), ("spills", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class gwfa_graph_info(ctypes.Structure):
@@ -60,12 +60,13 @@ class gwfa_graph_info(ctypes.Structure):
 
 
 class gwfa_tier(ctypes.Structure):
-    _fields_ = [("ctas", ctypes.c_uint32), ("log2_tiles", ctypes.c_uint32)]
+    _fields_ = [("ctas", ctypes.c_uint32), ("log2_tiles", ctypes.c_uint32),
+                ("threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class gwfa_engine_config(ctypes.Structure):
     _fields_ = [("n_tiers", ctypes.c_uint32), ("tiers", gwfa_tier * GWFA_MAX_TIERS),
-                ("threads", ctypes.c_uint32), ("prune_slabs", ctypes.c_uint32),
+                ("wide", gwfa_tier), ("threads", ctypes.c_uint32), ("prune_slabs", ctypes.c_uint32),
                 ("max_queries", ctypes.c_uint64), ("max_bases", ctypes.c_uint64)]
 
 
@@ -83,12 +84,16 @@ SIGNATURES = {
     "gwfa_engine_create": ([_P, ctypes.POINTER(gwfa_engine_config), ctypes.POINTER(_P)], ctypes.c_int),
     "gwfa_engine_destroy": ([_P], ctypes.c_int),
     "gwfa_engine_device_bytes": ([_P], _u64),
-    "gwfa_align_batch": ([_P, _u32, _P, _P, _P, _P, _P, ctypes.POINTER(gwfa_opts), _P, _P], ctypes.c_int),
+    "gwfa_align_batch": ([_P, _u32, _P, _P, _P, _P, _P, _u32, ctypes.POINTER(gwfa_opts), _P, _P],
+                         ctypes.c_int),
     "gwfa_pack_queries_device": ([_u32, _P, _P, _P, _P, _P], ctypes.c_int),
-    "gwfa_align_batch_device": ([_P, _u32, _P, _P, _P, _P, _P, _P, ctypes.POINTER(gwfa_opts), _P, _P],
-                                ctypes.c_int),
+    "gwfa_align_batch_device": ([_P, _u32, _P, _P, _P, _P, _P, _u32, _P, ctypes.POINTER(gwfa_opts), _P,
+                                 _P], ctypes.c_int),
     "gwfa_engine_last_launches": ([_P], _u32),
+    "gwfa_engine_set_stats": ([_P, _P], ctypes.c_int),
 }
+STAT_FIELDS = ("extend_ns", "expand_ns", "rounds", "extend_tiles", "expand_tiles", "max_tiles",
+               "hash_tiles", "scores")
 
 _lib = None
 
@@ -208,8 +213,12 @@ class Engine:
     def last_launches(self) -> int:
         return int(load().gwfa_engine_last_launches(self.handle))
 
+    def set_stats(self, d_stats: int | None):
+        """Per-query statistics into device memory (8 uint64 per query id), or None to stop."""
+        _check(load().gwfa_engine_set_stats(self.handle, d_stats or None), "gwfa_engine_set_stats")
+
     def align_batch(self, seq, off, v_s, v_e, order=None, max_lag: int = 0, max_score: int = -1,
-                    stream: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+                    stream: int = 0, out: np.ndarray | None = None, n_wide: int = 0) -> np.ndarray:
         """Host buffers in, host results out (gwfa_align_batch)."""
         seq = _c(seq, np.uint8)
         off = _c(off, np.uint64)
@@ -220,18 +229,18 @@ class Engine:
         o = _opts(max_lag, max_score)
         od = None if order is None else _c(order, np.uint32)
         _check(load().gwfa_align_batch(self.handle, n, seq.ctypes.data, off.ctypes.data, vs.ctypes.data,
-                                       ve.ctypes.data, None if od is None else od.ctypes.data,
+                                       ve.ctypes.data, None if od is None else od.ctypes.data, n_wide,
                                        ctypes.byref(o), res.ctypes.data, stream or None),
                "gwfa_align_batch")
         return res
 
     def align_batch_device(self, n: int, d_words: int, d_q_off: int, d_v_s: int, d_v_e: int,
                            d_order: int | None, d_status: int | None, d_out: int,
-                           max_lag: int = 0, max_score: int = -1, stream: int = 0):
+                           max_lag: int = 0, max_score: int = -1, stream: int = 0, n_wide: int = 0):
         """Device pointers in and out, asynchronous on `stream` (gwfa_align_batch_device)."""
         o = _opts(max_lag, max_score)
         _check(load().gwfa_align_batch_device(self.handle, n, d_words, d_q_off, d_v_s, d_v_e,
-                                              d_order or None, d_status or None, ctypes.byref(o),
+                                              d_order or None, n_wide, d_status or None, ctypes.byref(o),
                                               d_out, stream or None),
                "gwfa_align_batch_device")
 
@@ -279,14 +288,14 @@ class DeviceBatch:
         pack_queries_device(self.n, self.q.data_ptr(), self.q_off.data_ptr(), self.words.data_ptr(),
                             self.status.data_ptr(), st.cuda_stream)
 
-    def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None):
+    def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None, n_wide: int = 0):
         import torch
         st = stream if stream is not None else torch.cuda.current_stream(self.q.device)
         engine.align_batch_device(self.n, self.words.data_ptr(), self.q_off.data_ptr(),
                                   self.v_s.data_ptr(), self.v_e.data_ptr(),
                                   None if self.order is None else self.order.data_ptr(),
                                   self.status.data_ptr(), self.out.data_ptr(), max_lag, max_score,
-                                  st.cuda_stream)
+                                  st.cuda_stream, n_wide)
 
     def results(self) -> np.ndarray:
         return self.out.cpu().numpy().view(RESULT_DTYPE)

@@ -169,18 +169,17 @@ int gwfa_graph_create(uint32_t nv, const char *h_seq, const uint64_t *h_seq_off,
 
     int st = cuda_status(cudaSetDevice(device));
     if (st) { delete g; return st; }
+    std::vector<uint4> vinfo(nv);
+    for (uint32_t v = 0; v < nv; ++v)
+        vinfo[v] = make_uint4(vstart[v], vlen[v], g->h_arc_off[v], g->h_arc_off[v + 1]);
     st = dmalloc(&g->d_words, g->n_words * 4);
-    if (!st) st = dmalloc(&g->d_vstart, (uint64_t)nv * 4);
-    if (!st) st = dmalloc(&g->d_vlen, (uint64_t)nv * 4);
-    if (!st) st = dmalloc(&g->d_arc_off, (uint64_t)(nv + 1) * 4);
+    if (!st) st = dmalloc(&g->d_vinfo, (uint64_t)nv * sizeof(uint4));
     if (!st) st = dmalloc(&g->d_arc_dst, std::max<uint64_t>(g->na, 1) * 4);
     if (!st) st = cuda_status(cudaMemcpy(g->d_words, words.data(), g->n_words * 4, cudaMemcpyHostToDevice));
-    if (!st) st = cuda_status(cudaMemcpy(g->d_vstart, vstart.data(), (uint64_t)nv * 4, cudaMemcpyHostToDevice));
-    if (!st) st = cuda_status(cudaMemcpy(g->d_vlen, vlen.data(), (uint64_t)nv * 4, cudaMemcpyHostToDevice));
-    if (!st) st = cuda_status(cudaMemcpy(g->d_arc_off, g->h_arc_off.data(), (uint64_t)(nv + 1) * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cuda_status(cudaMemcpy(g->d_vinfo, vinfo.data(), (uint64_t)nv * sizeof(uint4), cudaMemcpyHostToDevice));
     if (!st && g->na) st = cuda_status(cudaMemcpy(g->d_arc_dst, g->h_arc_dst.data(), g->na * 4, cudaMemcpyHostToDevice));
     if (!st) st = cuda_status(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
-    g->device_bytes = g->n_words * 4 + (uint64_t)nv * 8 + (uint64_t)(nv + 1) * 4 + g->na * 4;
+    g->device_bytes = g->n_words * 4 + (uint64_t)nv * sizeof(uint4) + g->na * 4;
     if (st) { gwfa_graph_destroy(g); return st; }
     *out = g;
     return GWFA_OK;
@@ -190,9 +189,7 @@ int gwfa_graph_destroy(gwfa_graph *g) {
     if (!g) return GWFA_ERR_INVALID;
     cudaSetDevice(g->device);
     cudaFree(g->d_words);
-    cudaFree(g->d_vstart);
-    cudaFree(g->d_vlen);
-    cudaFree(g->d_arc_off);
+    cudaFree(g->d_vinfo);
     cudaFree(g->d_arc_dst);
     cudaFree(g->plain_slab);
     cudaFree(g->plain_stage);
@@ -257,7 +254,7 @@ int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, ui
             const uint64_t bytes = gwfa::slab_layout(log2, prune).total;
             st = dmalloc(&g->plain_slab, bytes);
             if (st) return st;
-            st = cuda_status(gwfa::launch_fill(g->plain_slab, bytes, s));
+            st = cuda_status(gwfa::launch_slab_init(g->plain_slab, bytes, 1, log2, prune, s));
             if (st) return st;
             g->plain_log2 = log2;
             g->plain_prune = prune;
@@ -288,12 +285,12 @@ int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, ui
         a.log2cap = log2;
         a.max_lag = o.max_lag;
         a.max_score = o.max_score;
-        st = cuda_status(gwfa::launch_align(a, prune, 1, 128, s));
+        st = cuda_status(gwfa::launch_align(a, prune, 1, 512, s));
         if (st) return st;
         st = cuda_status(cudaMemcpyAsync(out, d_res, sizeof(gwfa_result), cudaMemcpyDeviceToHost, s));
         if (!st) st = cuda_status(cudaStreamSynchronize(s));
         if (st) return st;
-        if (out->status == GWFA_ERR_CAPACITY && log2 < 24) {
+        if (out->status == GWFA_ERR_CAPACITY && log2 + 3 <= gwfa::kMaxLog2Tiles) {
             log2 += 3;   // grow the workspace and run again
             continue;
         }
@@ -311,12 +308,15 @@ int gwfa_engine_default_config(const gwfa_graph *g, int prune, gwfa_engine_confi
     int sms = 0, bps = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
         return GWFA_ERR_CUDA;
-    cfg->threads = 128;
+    // 512-thread CTAs, as many as fit on an SM (the kernel is bound by the latency
+    // of dependent L2 round trips, so resident warps matter more than registers)
+    cfg->threads = 512;
     if (gwfa::align_occupancy(prune != 0, cfg->threads, &bps) || bps < 1) bps = 1;
+    cfg->wide = {0u, prune ? 18u : 19u, 512u, 0u};   // no separate wide class by default
     cfg->n_tiers = 3;
-    cfg->tiers[0] = {(uint32_t)(sms * bps), prune ? 15u : 16u};
-    cfg->tiers[1] = {(uint32_t)sms, 19u};
-    cfg->tiers[2] = {(uint32_t)std::max(sms / 16, 1), 22u};
+    cfg->tiers[0] = {(uint32_t)(sms * bps), prune ? 15u : 16u, 0u, 0u};
+    cfg->tiers[1] = {(uint32_t)sms, 19u, 0u, 0u};
+    cfg->tiers[2] = {(uint32_t)std::max(sms / 8, 1), 22u, 0u, 0u};
     cfg->prune_slabs = prune ? 1 : 0;
     cfg->max_queries = 1 << 16;
     cfg->max_bases = 1ull << 28;
@@ -327,6 +327,10 @@ int gwfa_engine_destroy(gwfa_engine *e) {
     if (!e) return GWFA_ERR_INVALID;
     cudaSetDevice(e->g->device);
     for (int t = 0; t < GWFA_MAX_TIERS; ++t) cudaFree(e->slabs[t]);
+    cudaFree(e->wide_slabs);
+    if (e->side) cudaStreamDestroy(e->side);
+    if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    if (e->ev_join) cudaEventDestroy(e->ev_join);
     cudaFree(e->counters);
     cudaFree(e->retry_lists);
     cudaFree(e->stage);
@@ -352,9 +356,14 @@ int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_
     if (cfg->n_tiers < 1 || cfg->n_tiers > GWFA_MAX_TIERS) return GWFA_ERR_INVALID;
     const uint32_t threads = cfg->threads ? cfg->threads : 128;
     if (threads % 32 || threads < 64 || threads > 512) return GWFA_ERR_INVALID;
-    for (uint32_t t = 0; t < cfg->n_tiers; ++t)
-        if (cfg->tiers[t].ctas == 0 || cfg->tiers[t].log2_tiles < 8 || cfg->tiers[t].log2_tiles > 28)
+    for (uint32_t t = 0; t <= cfg->n_tiers; ++t) {
+        const gwfa_tier &tt = t < cfg->n_tiers ? cfg->tiers[t] : cfg->wide;
+        if (t == cfg->n_tiers && tt.ctas == 0) break;   // no wide CTAs
+        const uint32_t th = tt.threads;
+        if (tt.ctas == 0 || tt.log2_tiles < 8 || tt.log2_tiles > gwfa::kMaxLog2Tiles ||
+            (th && (th % 32 || th < 64 || th > 512)))
             return GWFA_ERR_INVALID;
+    }
     int st = cuda_status(cudaSetDevice(g->device));
     if (st) return st;
     gwfa_engine *e = new (std::nothrow) gwfa_engine();
@@ -367,9 +376,25 @@ int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_
         e->slab_bytes[t] = gwfa::slab_layout(cfg->tiers[t].log2_tiles, cfg->prune_slabs != 0).total;
         const uint64_t bytes = e->slab_bytes[t] * cfg->tiers[t].ctas;
         st = dmalloc(&e->slabs[t], bytes);
-        if (!st) st = cuda_status(gwfa::launch_fill(e->slabs[t], bytes, e->stream));
+        if (!st)
+            st = cuda_status(gwfa::launch_slab_init(e->slabs[t], e->slab_bytes[t], cfg->tiers[t].ctas,
+                                                    cfg->tiers[t].log2_tiles, cfg->prune_slabs != 0,
+                                                    e->stream));
         e->device_bytes += bytes;
     }
+    if (!st && cfg->wide.ctas) {
+        e->wide_slab_bytes = gwfa::slab_layout(cfg->wide.log2_tiles, cfg->prune_slabs != 0).total;
+        const uint64_t bytes = e->wide_slab_bytes * cfg->wide.ctas;
+        st = dmalloc(&e->wide_slabs, bytes);
+        if (!st)
+            st = cuda_status(gwfa::launch_slab_init(e->wide_slabs, e->wide_slab_bytes, cfg->wide.ctas,
+                                                    cfg->wide.log2_tiles, cfg->prune_slabs != 0,
+                                                    e->stream));
+        e->device_bytes += bytes;
+    }
+    if (!st) st = cuda_status(cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking));
+    if (!st) st = cuda_status(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming));
+    if (!st) st = cuda_status(cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming));
     if (!st) st = dmalloc(&e->counters, 256);
     if (!st) st = engine_retry_capacity(e, cfg->max_queries);
     if (!st) st = cuda_status(cudaStreamSynchronize(e->stream));
@@ -384,6 +409,13 @@ uint64_t gwfa_engine_device_bytes(const gwfa_engine *e) {
 
 uint32_t gwfa_engine_last_launches(const gwfa_engine *e) { return e ? e->last_launches : 0; }
 
+int gwfa_engine_set_stats(gwfa_engine *e, uint64_t *d_stats) {
+    if (!e) return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->stats = (unsigned long long *)d_stats;
+    return GWFA_OK;
+}
+
 int gwfa_pack_queries_device(uint32_t n_queries, const char *d_q, const uint64_t *d_q_off,
                              uint32_t *d_words, int32_t *d_status, void *stream) {
     if (!d_q_off || !d_words || (n_queries && !d_q)) return GWFA_ERR_INVALID;
@@ -393,17 +425,56 @@ int gwfa_pack_queries_device(uint32_t n_queries, const char *d_q, const uint64_t
 
 static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const uint64_t *d_q_off,
                      const uint32_t *d_vs, const uint32_t *d_ve, const uint32_t *d_order,
-                     const int32_t *d_status, const gwfa_opts &o, gwfa_result *d_out,
-                     cudaStream_t s) {
+                     uint32_t n_wide, const int32_t *d_status, const gwfa_opts &o,
+                     gwfa_result *d_out, cudaStream_t s) {
     int st = engine_retry_capacity(e, n);
     if (st) return st;
     const uint32_t T = e->cfg.n_tiers;
     uint32_t *heads = e->counters, *rcount = e->counters + GWFA_MAX_TIERS;
+    uint32_t *wide_head = e->counters + 2 * GWFA_MAX_TIERS;
     st = cuda_status(cudaMemsetAsync(e->counters, 0, 256, s));
     if (st) return st;
     const bool prune = o.max_lag > 0;
     e->last_launches = 0;
+    if (!e->wide_slabs) n_wide = 0;
+    n_wide = std::min(n_wide, n);
+    if (n_wide > 0) {
+        // the heaviest queries on wide CTAs, concurrently with tier 0 on the rest;
+        // their capacity failures join tier 0's retry list
+        TierArgs a{};
+        a.g = e->g->dev();
+        a.qwords = d_words;
+        a.q_off = d_q_off;
+        a.v_s = d_vs;
+        a.v_e = d_ve;
+        a.qstatus = d_status;
+        a.out = d_out;
+        a.list = d_order;
+        a.list_count = nullptr;
+        a.count_val = n_wide;
+        a.list_offset = 0;
+        a.retry = T > 1 ? e->retry_lists : nullptr;
+        a.retry_count = rcount;
+        a.head = wide_head;
+        a.slabs = e->wide_slabs;
+        a.slab_bytes = e->wide_slab_bytes;
+        a.log2cap = e->cfg.wide.log2_tiles;
+        a.max_lag = o.max_lag;
+        a.max_score = o.max_score;
+        a.stats = e->stats;
+        st = cuda_status(cudaEventRecord(e->ev_fork, s));
+        if (!st) st = cuda_status(cudaStreamWaitEvent(e->side, e->ev_fork, 0));
+        const uint32_t th = e->cfg.wide.threads ? e->cfg.wide.threads : e->cfg.threads;
+        if (!st) st = cuda_status(gwfa::launch_align(a, prune, e->cfg.wide.ctas, th, e->side));
+        if (!st) st = cuda_status(cudaEventRecord(e->ev_join, e->side));
+        if (st) return st;
+        e->last_launches++;
+    }
     for (uint32_t t = 0; t < T; ++t) {
+        if (t == 1 && n_wide > 0) {
+            st = cuda_status(cudaStreamWaitEvent(s, e->ev_join, 0));
+            if (st) return st;
+        }
         TierArgs a{};
         a.g = e->g->dev();
         a.qwords = d_words;
@@ -414,7 +485,8 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
         a.out = d_out;
         a.list = t == 0 ? d_order : e->retry_lists + (uint64_t)(t - 1) * e->retry_cap;
         a.list_count = t == 0 ? nullptr : rcount + (t - 1);
-        a.count_val = n;
+        a.count_val = t == 0 ? n - n_wide : n;
+        a.list_offset = t == 0 ? n_wide : 0;
         a.retry = t + 1 < T ? e->retry_lists + (uint64_t)t * e->retry_cap : nullptr;
         a.retry_count = rcount + t;
         a.head = heads + t;
@@ -423,16 +495,22 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
         a.log2cap = e->cfg.tiers[t].log2_tiles;
         a.max_lag = o.max_lag;
         a.max_score = o.max_score;
-        st = cuda_status(gwfa::launch_align(a, prune, e->cfg.tiers[t].ctas, e->cfg.threads, s));
+        a.stats = e->stats;
+        const uint32_t th = e->cfg.tiers[t].threads ? e->cfg.tiers[t].threads : e->cfg.threads;
+        st = cuda_status(gwfa::launch_align(a, prune, e->cfg.tiers[t].ctas, th, s));
         if (st) return st;
         e->last_launches++;
+    }
+    if (T == 1 && n_wide > 0) {
+        st = cuda_status(cudaStreamWaitEvent(s, e->ev_join, 0));
+        if (st) return st;
     }
     return GWFA_OK;
 }
 
 int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
                             const uint64_t *d_q_off, const uint32_t *d_vs, const uint32_t *d_ve,
-                            const uint32_t *d_order, const int32_t *d_status,
+                            const uint32_t *d_order, uint32_t n_wide, const int32_t *d_status,
                             const gwfa_opts *opts, gwfa_result *d_out, void *stream) {
     if (!e || !d_words || !d_q_off || !d_vs || !d_ve || !d_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
@@ -443,12 +521,12 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
     int st = cuda_status(cudaSetDevice(e->g->device));
     if (st) return st;
     cudaStream_t s = stream ? (cudaStream_t)stream : e->stream;
-    return run_tiers(e, n, d_words, d_q_off, d_vs, d_ve, d_order, d_status, o, d_out, s);
+    return run_tiers(e, n, d_words, d_q_off, d_vs, d_ve, d_order, n_wide, d_status, o, d_out, s);
 }
 
 int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t *h_q_off,
                      const uint32_t *h_vs, const uint32_t *h_ve, const uint32_t *h_order,
-                     const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
+                     uint32_t n_wide, const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
     if (!e || !h_q_off || !h_vs || !h_ve || !h_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
     if (o.max_lag < 0 || o.traceback != 0) return GWFA_ERR_INVALID;
@@ -482,7 +560,9 @@ int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t
     if (!st) st = cuda_status(cudaMemcpyAsync(d_ve, h_ve, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
     if (!st && h_order) st = cuda_status(cudaMemcpyAsync(d_order, h_order, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
     if (!st) st = cuda_status(gwfa::launch_pack(n, d_q, d_off, d_words, d_status, s));
-    if (!st) st = run_tiers(e, n, d_words, d_off, d_vs, d_ve, h_order ? d_order : nullptr, d_status, o, d_out, s);
+    if (!st)
+        st = run_tiers(e, n, d_words, d_off, d_vs, d_ve, h_order ? d_order : nullptr, n_wide, d_status, o,
+                       d_out, s);
     if (!st) e->last_launches += 1;
     if (!st) st = cuda_status(cudaMemcpyAsync(h_out, d_out, (uint64_t)n * sizeof(gwfa_result), cudaMemcpyDeviceToHost, s));
     if (!st) st = cuda_status(cudaStreamSynchronize(s));

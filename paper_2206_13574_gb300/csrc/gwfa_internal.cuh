@@ -19,38 +19,67 @@ constexpr uint64_t kEmptyKey = ~0ull;
 // Packed graph resident on the device (a1): labels 2-bit packed, base t of a word
 // in bits 2t..2t+1, every vertex starting on a word boundary, 2 zero pad words at
 // the end so that a 32-base window may always read two consecutive words.
+// vinfo[v] = {first word of the label, |v|, first out-arc, end of out-arcs}: one
+// 16-byte load gives everything the extension of a diagonal of v needs.
 struct DevGraph {
     const uint32_t *words;
-    const uint32_t *vstart;   // word index of each label
-    const uint32_t *vlen;     // |v|
-    const uint32_t *arc_off;  // CSR of out-arcs, nv + 1
+    const uint4 *vinfo;
     const uint32_t *arc_dst;
     uint32_t nv;
 };
 
+// List entry: tile slot, vertex, tile index kb (diagonals 8kb .. 8kb+7).
+struct __align__(16) LEnt {
+    uint32_t slot;
+    uint32_t v;
+    int32_t kb;
+    uint32_t pad;
+};
+// Extended-frontier header: slot | live-lane mask << 24, vertex, kb, |v|.
+struct __align__(16) EHdr {
+    uint32_t slot_mask;
+    uint32_t v;
+    int32_t kb;
+    uint32_t lv;
+};
+constexpr uint32_t kMaxLog2Tiles = 24;   // slot must fit the 24 low bits of EHdr
+
+// Hash slot of one tile, one 64-byte line in exact mode (128 in pruning mode):
+// key (v << 32 | kb, all ones = empty), the two lane-mask words of the phase
+// parities, and the 8 offsets.  A tile visit touches a single line.
+template <class T>
+struct alignas(sizeof(T) == 4 ? 64 : 128) SlotT {
+    unsigned long long key;
+    uint32_t reg[2];
+    T vals[kTile];
+};
+// Extended-frontier entry: header + snapshot of the 8 offsets after extension.
+template <class T>
+struct alignas(sizeof(T) == 4 ? 64 : 128) EEntT {
+    EHdr hdr;
+    T vals[kTile];
+};
+
 // Per-CTA slab layout (all arrays 256-byte aligned), cap = 2^log2 tiles.
 struct SlabLayout {
-    uint64_t keys, reg0, reg1, vals, touched, qlist, slist0, slist1, eslot, emask, evals, req, total;
+    uint64_t slots, touched, qlist, slist0, slist1, elist, req, total, slot_bytes;
 };
 
 __host__ __device__ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 __host__ __device__ inline SlabLayout slab_layout(uint32_t log2cap, bool prune) {
     const uint64_t cap = 1ull << log2cap;
-    const uint64_t vb = prune ? 8 : 4;
+    const uint64_t sb = prune ? sizeof(SlotT<long long>) : sizeof(SlotT<int>);
+    const uint64_t eb = prune ? sizeof(EEntT<long long>) : sizeof(EEntT<int>);
     SlabLayout L;
     uint64_t o = 0;
-    L.keys = o;    o = align256(o + cap * 8);
-    L.reg0 = o;    o = align256(o + cap * 8);
-    L.reg1 = o;    o = align256(o + cap * 8);
-    L.vals = o;    o = align256(o + cap * kTile * vb);
+    L.slot_bytes = sb;
+    L.slots = o;   o = align256(o + cap * sb);
     L.touched = o; o = align256(o + cap * 4);
-    L.qlist = o;   o = align256(o + cap * 4);
-    L.slist0 = o;  o = align256(o + cap * 4);
-    L.slist1 = o;  o = align256(o + cap * 4);
-    L.eslot = o;   o = align256(o + cap * 4);
-    L.emask = o;   o = align256(o + cap * 4);
-    L.evals = o;   o = align256(o + cap * kTile * vb);
+    L.qlist = o;   o = align256(o + cap * sizeof(LEnt));
+    L.slist0 = o;  o = align256(o + cap * sizeof(LEnt));
+    L.slist1 = o;  o = align256(o + cap * sizeof(LEnt));
+    L.elist = o;   o = align256(o + cap * eb);
     L.req = o;     o = align256(o + (prune ? cap * 16 : 0));
     L.total = o;
     return L;
@@ -67,6 +96,7 @@ struct TierArgs {
     const uint32_t *list;       // query ids to run (NULL: identity)
     const uint32_t *list_count; // device count (NULL: use count_val)
     uint32_t count_val;
+    uint32_t list_offset;       // queue position t runs list[list_offset + t]
     uint32_t *retry;            // overflowing query ids for the next tier (NULL: last tier)
     uint32_t *retry_count;
     uint32_t *head;             // work-queue head
@@ -75,7 +105,9 @@ struct TierArgs {
     uint32_t log2cap;
     int32_t max_lag;
     int32_t max_score;
+    unsigned long long *stats;  // optional, kStatWords per query id (see gwfa_engine_set_stats)
 };
+constexpr int kStatWords = 8;
 
 // launchers (gwfa_kernels.cu)
 cudaError_t launch_align(const TierArgs &a, bool prune, uint32_t ctas, uint32_t threads,
@@ -83,6 +115,8 @@ cudaError_t launch_align(const TierArgs &a, bool prune, uint32_t ctas, uint32_t 
 cudaError_t launch_pack(uint32_t nq, const char *d_q, const uint64_t *d_off, uint32_t *d_words,
                         int32_t *d_status, cudaStream_t st);
 cudaError_t launch_fill(void *p, uint64_t bytes, cudaStream_t st);
+cudaError_t launch_slab_init(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_slabs, uint32_t log2cap,
+                             bool prune, cudaStream_t st);
 int align_occupancy(bool prune, uint32_t threads, int *blocks_per_sm);
 
 }  // namespace gwfa
@@ -94,8 +128,8 @@ struct gwfa_graph {
     uint32_t max_outdeg = 0;
     int has_cycles = 0;
     std::vector<uint32_t> h_arc_off, h_arc_dst;
-    uint32_t *d_words = nullptr, *d_vstart = nullptr, *d_vlen = nullptr, *d_arc_off = nullptr,
-             *d_arc_dst = nullptr;
+    uint32_t *d_words = nullptr, *d_arc_dst = nullptr;
+    uint4 *d_vinfo = nullptr;
     uint64_t device_bytes = 0;
     // plain-path workspace (one slab), guarded by mu
     mutable std::mutex mu;
@@ -106,7 +140,7 @@ struct gwfa_graph {
     mutable uint64_t plain_stage_bytes = 0;
     mutable cudaStream_t stream = nullptr;
     gwfa::DevGraph dev() const {
-        return gwfa::DevGraph{d_words, d_vstart, d_vlen, d_arc_off, d_arc_dst, nv};
+        return gwfa::DevGraph{d_words, d_vinfo, d_arc_dst, nv};
     }
 };
 
@@ -115,6 +149,10 @@ struct gwfa_engine {
     gwfa_engine_config cfg{};
     uint8_t *slabs[GWFA_MAX_TIERS] = {};
     uint64_t slab_bytes[GWFA_MAX_TIERS] = {};
+    uint8_t *wide_slabs = nullptr;
+    uint64_t wide_slab_bytes = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint32_t *counters = nullptr;   // per tier: head, retry_count; plus retry lists
     uint32_t *retry_lists = nullptr;
     uint64_t retry_cap = 0;
@@ -124,5 +162,6 @@ struct gwfa_engine {
     cudaStream_t stream = nullptr;
     uint64_t device_bytes = 0;
     uint32_t last_launches = 0;
+    unsigned long long *stats = nullptr;
     std::mutex mu;
 };

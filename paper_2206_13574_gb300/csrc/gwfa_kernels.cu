@@ -12,18 +12,20 @@
 //          base = spelled walk length before v, so W~ = base + j); absent = -1.
 //          Entries persist for the whole query (an entry blocks re-spilling,
 //          Alg. 2) and are wiped through the `touched` list when it ends.
-//   reg    two words per tile, used alternately by successive phases:
-//          (phase stamp << 32 | lane mask).  The first lane to register a tile in
-//          a phase appends the tile to that phase's list, so every list holds a
-//          tile once, with the mask of its live diagonals.
+//   reg    two lane-mask words per tile, one per phase parity.  A phase that
+//          makes lanes live ORs their bits into its parity; the lane that finds
+//          the word 0 appends the tile to that phase's list; the next phase takes
+//          the mask with an exchange to 0, so each list holds every tile once.
 //   Q      qlist: tiles live after GwfExpand (the queue Q of Alg. 1-3).
-//   spill  slist[2]: tiles that received offset 0 by a spill in the current
-//          extension round; they are extended in the same score (Alg. 2 pushes
-//          them onto the queue being drained).
-//   E      the extended frontier (Q' of Alg. 2): tile, mask and a snapshot of the
-//          8 offsets after extension.  GwfExpand reads the snapshot, so its
-//          sources are the offsets before any of its own writes (the H~ / H~'
-//          split of Alg. 3) and it can max-merge straight into H~ with atomics.
+//   spill  slist[2]: tiles that received offset 0 by a spill and still have to
+//          be extended in this score (Alg. 2 pushes them onto the queue being
+//          drained).  Exact mode extends a won spill depth-first in the thread
+//          that won it and only overflows to these lists; pruning mode goes
+//          breadth first (see extend_round_prune).
+//   E      the extended frontier (Q' of Alg. 2): header (slot, mask, v, kb, |v|)
+//          and a snapshot of the 8 offsets after extension.  GwfExpand reads the
+//          snapshot, so its sources are the offsets before any of its own writes
+//          (the H~ / H~' split of Alg. 3) and it max-merges straight into H~.
 //
 // Order independence (why parallel execution gives the paper's exact result and
 // work counts): in Alg. 2 every diagonal of the closure is extended exactly once
@@ -43,6 +45,7 @@ namespace {
 
 constexpr long long kTagPend = 0, kTagFresh = 1, kTagSettled = 2;
 constexpr uint32_t kBaseMask = 0x3FFFFFFFu;
+constexpr int kStack = 6;   // depth-first spill stack per thread (exact mode)
 
 template <bool P> struct VT;
 template <> struct VT<false> { using T = int; };
@@ -58,11 +61,10 @@ __device__ __forceinline__ uint32_t pbase(int) { return 0; }
 
 template <bool P> struct Slab {
     using T = typename VT<P>::T;
-    unsigned long long *keys;
-    unsigned long long *reg[2];
-    T *vals;
-    uint32_t *touched, *qlist, *slist[2], *eslot, *emask;
-    T *evals;
+    SlotT<T> *slots;
+    uint32_t *touched;
+    LEnt *qlist, *slist[2];
+    EEntT<T> *elist;
     int4 *req;
     uint32_t cap, mask;
 };
@@ -71,17 +73,12 @@ template <bool P>
 __device__ __forceinline__ Slab<P> carve(uint8_t *base, uint32_t log2cap) {
     SlabLayout L = slab_layout(log2cap, P);
     Slab<P> s;
-    s.keys = (unsigned long long *)(base + L.keys);
-    s.reg[0] = (unsigned long long *)(base + L.reg0);
-    s.reg[1] = (unsigned long long *)(base + L.reg1);
-    s.vals = (typename VT<P>::T *)(base + L.vals);
+    s.slots = (SlotT<typename VT<P>::T> *)(base + L.slots);
     s.touched = (uint32_t *)(base + L.touched);
-    s.qlist = (uint32_t *)(base + L.qlist);
-    s.slist[0] = (uint32_t *)(base + L.slist0);
-    s.slist[1] = (uint32_t *)(base + L.slist1);
-    s.eslot = (uint32_t *)(base + L.eslot);
-    s.emask = (uint32_t *)(base + L.emask);
-    s.evals = (typename VT<P>::T *)(base + L.evals);
+    s.qlist = (LEnt *)(base + L.qlist);
+    s.slist[0] = (LEnt *)(base + L.slist0);
+    s.slist[1] = (LEnt *)(base + L.slist1);
+    s.elist = (EEntT<typename VT<P>::T> *)(base + L.elist);
     s.req = (int4 *)(base + L.req);
     s.cap = 1u << log2cap;
     s.mask = s.cap - 1;
@@ -95,7 +92,7 @@ struct Sh {
     int found;
     uint32_t nq[2];     // Q list length, by parity of the score that consumes it
     uint32_t ns[3];     // spill list length, rotating over three rounds (see align_one)
-    uint32_t nreq[2];   // pending spill requests (pruning mode), by generation parity
+    uint32_t nreq[2];   // pending spill requests (pruning mode), by round parity
     uint32_t ne;        // extended-frontier entries this score
     uint32_t nt;        // tiles claimed (touched) this query
     uint32_t score_cells;
@@ -105,6 +102,24 @@ struct Sh {
 };
 
 __device__ __forceinline__ void set_err(Sh &sh, int code) { atomicCAS(&sh.err, 0, code); }
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ LEnt ld_lent(const LEnt *p) {
+    const uint4 x = __ldcg((const uint4 *)p);
+    return LEnt{x.x, x.y, (int32_t)x.z, x.w};
+}
+__device__ __forceinline__ EHdr ld_ehdr(const EHdr *p) {
+    const uint4 x = __ldcg((const uint4 *)p);
+    return EHdr{x.x, x.y, (int32_t)x.z, x.w};
+}
+__device__ __forceinline__ void st_ehdr(EHdr *p, uint32_t slot_mask, uint32_t v, int kb, uint32_t lv) {
+    __stcg((uint4 *)p, make_uint4(slot_mask, v, (uint32_t)kb, lv));
+}
 
 // 16 bases starting at base position p of a packed stream.
 __device__ __forceinline__ uint32_t window16(const uint32_t *__restrict__ w, uint64_t p) {
@@ -131,6 +146,24 @@ __device__ __forceinline__ int lcp(const uint32_t *__restrict__ qw, int i, int n
     return min(l, maxl);
 }
 
+// The same LCP when the first window XOR `x` (bases i.. against j..) is already
+// loaded, so that two diagonals can have their first windows in flight together.
+__device__ __forceinline__ int lcp_finish(const uint32_t *__restrict__ qw, int i,
+                                          const uint32_t *__restrict__ vw, int j, int maxl,
+                                          uint32_t x) {
+    int l = 0;
+    while (l < maxl) {
+        if (x) {
+            l += (__ffs(x) - 1) >> 1;
+            break;
+        }
+        l += 16;
+        if (l >= maxl) break;
+        x = window16(qw, (uint64_t)(i + l)) ^ window16(vw, (uint64_t)(j + l));
+    }
+    return min(l, maxl);
+}
+
 __device__ __forceinline__ unsigned long long tile_key(uint32_t v, int kb) {
     return ((unsigned long long)v << 32) | (uint32_t)kb;
 }
@@ -139,10 +172,10 @@ template <bool P>
 __device__ int find_or_insert(const Slab<P> &s, Sh &sh, unsigned long long key) {
     uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & s.mask;
     for (int probe = 0; probe < 256; ++probe) {
-        const unsigned long long cur = __ldcg(&s.keys[h]);
+        const unsigned long long cur = __ldcg(&s.slots[h].key);
         if (cur == key) return (int)h;
         if (cur == kEmptyKey) {
-            const unsigned long long prev = atomicCAS(&s.keys[h], kEmptyKey, key);
+            const unsigned long long prev = atomicCAS(&s.slots[h].key, kEmptyKey, key);
             if (prev == kEmptyKey) {
                 const uint32_t t = atomicAdd(&sh.nt, 1u);
                 s.touched[t] = h;   // t < cap: each claim takes a distinct empty slot
@@ -157,30 +190,16 @@ __device__ int find_or_insert(const Slab<P> &s, Sh &sh, unsigned long long key) 
     return -1;
 }
 
-// Register lane `bit` of a tile for phase `stamp`; true for the first lane of the
-// tile in this phase (that caller appends the tile to the phase's list).
-__device__ __forceinline__ bool reg_lane(unsigned long long *w, uint32_t stamp, uint32_t bit,
-                                         Sh &sh) {
-    unsigned long long old = __ldcg(w);
-    for (int it = 0; it < 64; ++it) {
-        if ((uint32_t)(old >> 32) == stamp) {
-            atomicOr(w, (unsigned long long)bit);
-            return false;
-        }
-        const unsigned long long nw = ((unsigned long long)stamp << 32) | bit;
-        const unsigned long long prev = atomicCAS(w, old, nw);
-        if (prev == old) return true;
-        old = prev;
+// Make lane `bit` of tile (slot, v, kb) live for the phase owning `regw`; the
+// first lane to do so appends the tile to that phase's list.
+__device__ __forceinline__ void reg_append(uint32_t *regw, LEnt *list, uint32_t *count,
+                                           uint32_t cap, uint32_t slot, uint32_t v, int kb,
+                                           uint32_t bit, Sh &sh) {
+    if (atomicOr(regw, bit) == 0u) {
+        const uint32_t i = atomicAdd(count, 1u);
+        if (i < cap) __stcg((uint4 *)&list[i], make_uint4(slot, v, (uint32_t)kb, 0u));
+        else set_err(sh, GWFA_ERR_CAPACITY);
     }
-    set_err(sh, GWFA_ERR_CAPACITY);
-    return false;
-}
-
-__device__ __forceinline__ void list_append(uint32_t *list, uint32_t *count, uint32_t cap,
-                                            uint32_t slot, Sh &sh) {
-    const uint32_t i = atomicAdd(count, 1u);
-    if (i < cap) list[i] = slot;
-    else set_err(sh, GWFA_ERR_CAPACITY);
 }
 
 struct QCtx {
@@ -188,196 +207,309 @@ struct QCtx {
     int n;
     uint32_t ve;
     int ke;
-    uint32_t lve;
 };
 
-// Offer value `cand` to diagonal lane `ln` of tile `slot` (GwfExpand's max-merge
-// into H~); registers the lane in the next Q if its offset strictly improved.
-template <bool P>
-__device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, int slot, int ln,
-                                      typename VT<P>::T cand, uint32_t stamp, int par,
-                                      uint32_t *qcount) {
-    const typename VT<P>::T prev = atomicMax(&s.vals[(uint32_t)slot * kTile + ln], cand);
-    if (prev < 0) atomicAdd(&sh.visited, 1ull);
-    if (pj(prev) < pj(cand)) {
-        if (reg_lane(&s.reg[par][slot], stamp, 1u << ln, sh))
-            list_append(s.qlist, qcount, s.cap, (uint32_t)slot, sh);
-    }
-}
-
-// Spill of Alg. 2: diagonal (v, k) reached |v|; offset 0 (with walk base
-// `base + |v|`) goes to (u, k + |v|) for every arc (v, u) where it is absent.
-template <bool P>
-__device__ void spill_arcs(const DevGraph &g, const Slab<P> &s, Sh &sh, uint32_t v, int k,
-                           uint32_t lv, uint32_t base, uint32_t stamp, int par,
-                           uint32_t *next_list, uint32_t *next_count) {
-    const uint32_t a0 = __ldg(&g.arc_off[v]), a1 = __ldg(&g.arc_off[v + 1]);
-    const int ku = k + (int)lv;
-    const uint32_t nb = base + lv;
-    if (P && nb > kBaseMask) { set_err(sh, GWFA_ERR_CAPACITY); return; }
-    for (uint32_t a = a0; a < a1; ++a) {
-        const uint32_t u = __ldg(&g.arc_dst[a]);
-        const int su = find_or_insert(s, sh, tile_key(u, ku >> 3));
-        if (su < 0) return;
-        const int ln = ku & 7;
-        typename VT<P>::T cand;
-        if constexpr (P) cand = pk(0, kTagPend, nb);
-        else cand = 0;
-        const typename VT<P>::T prev = atomicMax(&s.vals[(uint32_t)su * kTile + ln], cand);
-        if (prev < 0) {
-            atomicAdd(&sh.visited, 1ull);
-            atomicAdd(&sh.spills, 1ull);
-            if (reg_lane(&s.reg[par][su], stamp, 1u << ln, sh))
-                list_append(next_list, next_count, s.cap, (uint32_t)su, sh);
+// Exact mode: diagonal (v, k) reached |v| (Alg. 2 arc loop).  Offset 0 goes to
+// (u, k + |v|) for every arc (v, u) where it is absent; a diagonal this thread
+// inserts is extended by this thread at once, depth first, with its own arcs in
+// turn.  Only when the small stack is full does a won diagonal go to the spill
+// list of the next round instead.
+__device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const QCtx &q,
+                          uint32_t arc0, uint32_t arc1, int ku0, int next_par, LEnt *next_list,
+                          uint32_t *next_count) {
+    uint32_t st_slot[kStack], st_u[kStack];
+    int st_k[kStack];
+    int top = 0;
+    uint32_t a0 = arc0, a1 = arc1;
+    int ku = ku0;
+    for (;;) {
+        for (uint32_t a = a0; a < a1; ++a) {
+            const uint32_t u = __ldg(&g.arc_dst[a]);
+            const int su = find_or_insert(s, sh, tile_key(u, ku >> 3));
+            if (su < 0) return;
+            const int prev = atomicMax(&s.slots[su].vals[ku & 7], 0);
+            if (prev < 0) {
+                atomicAdd(&sh.visited, 1ull);
+                atomicAdd(&sh.spills, 1ull);
+                if (top < kStack) {
+                    st_slot[top] = (uint32_t)su;
+                    st_u[top] = u;
+                    st_k[top] = ku;
+                    ++top;
+                } else {
+                    reg_append(&s.slots[su].reg[next_par], next_list, next_count, s.cap, (uint32_t)su, u, ku >> 3,
+                               1u << (ku & 7), sh);
+                }
+            }
+        }
+        if (top == 0) return;
+        --top;
+        const uint32_t su = st_slot[top], u = st_u[top];
+        const int k = st_k[top];
+        const uint4 vi = __ldg(&g.vinfo[u]);
+        const int l = lcp(q.qw, k, q.n, g.words + vi.x, 0, (int)vi.y);
+        __stcg(&s.slots[su].vals[k & 7], l);
+        const uint32_t eidx = atomicAdd(&sh.ne, 1u);
+        atomicAdd(&sh.score_cells, 1u);
+        if (eidx < s.cap) {
+            st_ehdr(&s.elist[eidx].hdr, su | ((1u << (k & 7)) << 24), u, k >> 3, vi.y);
+            __stcg(&s.elist[eidx].vals[k & 7], l);
+        } else {
+            set_err(sh, GWFA_ERR_CAPACITY);
+        }
+        if (u == q.ve && k == q.ke && (uint32_t)l == vi.y) sh.found = 1;
+        if ((uint32_t)l == vi.y) {
+            a0 = vi.z;
+            a1 = vi.w;
+            ku = k + (int)vi.y;
+        } else {
+            a0 = a1 = 0;
         }
     }
 }
 
-// One extension round over `list` (tiles registered at phase `cur_stamp`).
-template <bool P>
-__device__ void extend_round(const DevGraph &g, const Slab<P> &s, Sh &sh, const QCtx &q,
-                             const uint32_t *list, uint32_t n_list, int cur_par,
-                             uint32_t next_stamp, int next_par, uint32_t *next_list,
-                             uint32_t *next_count, uint32_t *req_count) {
-    using T = typename VT<P>::T;
+// One extension round over `list` in exact mode.  Each 8-lane group takes two
+// tiles per iteration and keeps both dependency chains (list entry -> mask,
+// offsets, vertex info -> first LCP window) in flight together.
+__device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &sh, const QCtx &q,
+                                   const LEnt *list, uint32_t n_list, int par, int next_par,
+                                   LEnt *next_list, uint32_t *next_count) {
+    const int gid = threadIdx.x >> 3, ln = threadIdx.x & 7, ngroups = blockDim.x >> 3;
+    const unsigned gmask = 0xFFu << (threadIdx.x & 24);
+    for (uint32_t e0 = gid; e0 < n_list; e0 += 2 * ngroups) {
+        const bool has1 = e0 + ngroups < n_list;   // uniform within the group
+        LEnt ent[2];
+        ent[0] = ld_lent(&list[e0]);
+        ent[1] = has1 ? ld_lent(&list[e0 + ngroups]) : ent[0];
+        uint32_t m[2] = {0u, 0u};
+        int val[2];
+        uint4 vi[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (ln == 0 && (u == 0 || has1)) m[u] = atomicExch(&s.slots[ent[u].slot].reg[par], 0u);
+            val[u] = __ldcg(&s.slots[ent[u].slot].vals[ln]);
+            vi[u] = __ldg(&g.vinfo[ent[u].v]);
+        }
+        uint32_t eidx = 0;
+        m[0] = __shfl_sync(gmask, m[0], 0, 8);
+        m[1] = __shfl_sync(gmask, m[1], 0, 8);
+        if (ln == 0) {
+            eidx = atomicAdd(&sh.ne, has1 ? 2u : 1u);
+            atomicAdd(&sh.score_cells, (uint32_t)(__popc(m[0]) + __popc(m[1])));
+        }
+        eidx = __shfl_sync(gmask, eidx, 0, 8);
+        bool live[2];
+        int k[2], maxl[2];
+        uint32_t x[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            live[u] = (m[u] >> ln) & 1u;
+            k[u] = ent[u].kb * kTile + ln;
+            maxl[u] = 0;
+            x[u] = 0;
+            if (live[u]) {
+                const int i = k[u] + val[u];
+                maxl[u] = min(q.n - i, (int)vi[u].y - val[u]);
+                if (maxl[u] > 0)
+                    x[u] = window16(q.qw, (uint64_t)i) ^ window16(g.words + vi[u].x, (uint64_t)val[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !has1) break;
+            if (live[u]) {
+                val[u] += lcp_finish(q.qw, k[u] + val[u], g.words + vi[u].x, val[u], maxl[u], x[u]);
+                __stcg(&s.slots[ent[u].slot].vals[ln], val[u]);
+                if (ent[u].v == q.ve && k[u] == q.ke && (uint32_t)val[u] == vi[u].y) sh.found = 1;
+            }
+            const uint32_t ei = eidx + u;
+            if (ei < s.cap) {
+                if (ln == 0) st_ehdr(&s.elist[ei].hdr, ent[u].slot | (m[u] << 24), ent[u].v, ent[u].kb, vi[u].y);
+                __stcg(&s.elist[ei].vals[ln], live[u] ? val[u] : -1);
+            } else if (ln == 0) {
+                set_err(sh, GWFA_ERR_CAPACITY);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !has1) break;
+            if (live[u] && (uint32_t)val[u] == vi[u].y)
+                spill_dfs(g, s, sh, q, vi[u].z, vi[u].w, k[u] + (int)vi[u].y, next_par, next_list,
+                          next_count);
+        }
+    }
+}
+
+// One extension round over `list` in pruning mode.  Spills are recorded, not
+// applied: apply_spill_requests runs after the round's barrier, so a spill can
+// never touch a diagonal that was present before the round (Alg. 2's presence
+// test) and same-round spills into one diagonal merge by the larger walk base.
+__device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &sh, const QCtx &q,
+                                   const LEnt *list, uint32_t n_list, int par, uint32_t *req_count) {
     const int gid = threadIdx.x >> 3, ln = threadIdx.x & 7, ngroups = blockDim.x >> 3;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     for (uint32_t e = gid; e < n_list; e += ngroups) {
-        const uint32_t slot = __ldcg(&list[e]);
-        const unsigned long long key = __ldcg(&s.keys[slot]);
-        const uint32_t m = (uint32_t)__ldcg(&s.reg[cur_par][slot]) & 0xFFu;
-        const uint32_t v = (uint32_t)(key >> 32);
-        const int k = (int)(uint32_t)key * kTile + ln;
-        uint32_t eidx = 0;
+        const LEnt ent = ld_lent(&list[e]);
+        uint32_t m = 0, eidx = 0;
+        if (ln == 0) m = atomicExch(&s.slots[ent.slot].reg[par], 0u);
+        long long val = __ldcg(&s.slots[ent.slot].vals[ln]);
+        const uint4 vi = __ldg(&g.vinfo[ent.v]);
+        m = __shfl_sync(gmask, m, 0, 8);
         if (ln == 0) {
             eidx = atomicAdd(&sh.ne, 1u);
             atomicAdd(&sh.score_cells, (uint32_t)__popc(m));
         }
         eidx = __shfl_sync(gmask, eidx, 0, 8);
-        T val = (T)-1;
+        const int k = ent.kb * kTile + ln;
+        const bool live = (m >> ln) & 1u;
         unsigned long long a = 0;
-        if ((m >> ln) & 1u) {
-            val = __ldcg(&s.vals[slot * kTile + ln]);
+        if (live) {
             const int j = pj(val);
-            const uint32_t lv = __ldg(&g.vlen[v]);
             const int i = k + j;
-            const int l = lcp(q.qw, i, q.n, g.words + __ldg(&g.vstart[v]), j, (int)lv);
-            const int j2 = j + l;
-            if constexpr (P) val = pk(j2, kTagSettled, pbase(val));
-            else val = j2;
-            __stcg(&s.vals[slot * kTile + ln], val);
-            if (v == q.ve && k == q.ke && (uint32_t)j2 == lv) sh.found = 1;
-            if constexpr (P) a = (unsigned long long)(long long)(i + l) + pbase(val) + (unsigned)j2;
-            if ((uint32_t)j2 == lv) {
-                if constexpr (P) {
-                    const uint32_t r = atomicAdd(req_count, 1u);
-                    if (r < s.cap) s.req[r] = make_int4((int)v, k, (int)pbase(val), (int)lv);
-                    else set_err(sh, GWFA_ERR_CAPACITY);
-                } else {
-                    spill_arcs<P>(g, s, sh, v, k, lv, 0u, next_stamp, next_par, next_list,
-                                  next_count);
-                }
+            const int j2 = j + lcp(q.qw, i, q.n, g.words + vi.x, j, (int)vi.y);
+            val = pk(j2, kTagSettled, pbase(val));
+            __stcg(&s.slots[ent.slot].vals[ln], val);
+            if (ent.v == q.ve && k == q.ke && (uint32_t)j2 == vi.y) sh.found = 1;
+            a = (unsigned long long)(k + j2) + pbase(val) + (unsigned)j2;   // a = i + W~ (Alg. 4)
+            if ((uint32_t)j2 == vi.y) {
+                const uint32_t nb = pbase(val) + vi.y;
+                if (nb > kBaseMask) set_err(sh, GWFA_ERR_CAPACITY);
+                const uint32_t r = atomicAdd(req_count, 1u);
+                if (r < s.cap) __stcg(&s.req[r], make_int4(k + (int)vi.y, (int)nb, (int)vi.z, (int)vi.w));
+                else set_err(sh, GWFA_ERR_CAPACITY);
             }
         }
-        if constexpr (P) {
-            // a = i + W~ of Alg. 4, reduced over the tile then the CTA
-            for (int o = 4; o >= 1; o >>= 1) {
-                const unsigned long long b = __shfl_xor_sync(gmask, a, o, 8);
-                a = b > a ? b : a;
-            }
-            if (ln == 0 && a > 0) atomicMax(&sh.amax, a);
+        for (int o = 4; o >= 1; o >>= 1) {
+            const unsigned long long b = __shfl_xor_sync(gmask, a, o, 8);
+            a = b > a ? b : a;
         }
+        if (ln == 0 && a > 0) atomicMax(&sh.amax, a);
         if (eidx < s.cap) {
-            if (ln == 0) {
-                __stcg(&s.eslot[eidx], slot);
-                __stcg(&s.emask[eidx], m);
-            }
-            __stcg(&s.evals[eidx * kTile + ln], val);
+            if (ln == 0) st_ehdr(&s.elist[eidx].hdr, ent.slot | (m << 24), ent.v, ent.kb, vi.y);
+            __stcg(&s.elist[eidx].vals[ln], live ? val : -1ll);
         } else if (ln == 0) {
             set_err(sh, GWFA_ERR_CAPACITY);
         }
     }
 }
 
-// Pruning mode, second half of a round: apply the recorded spills after every
-// diagonal of the round has been extended, so that a spill can never touch a
-// diagonal that was present before the round (Alg. 2's presence test).
-__device__ void apply_spill_requests(const DevGraph &g, const Slab<true> &s, Sh &sh,
-                                     uint32_t n_req, uint32_t stamp, int par,
-                                     uint32_t *next_list, uint32_t *next_count) {
+// Pruning mode, second half of a round: offset 0 with walk base nb on (u, ku)
+// for every recorded spill; the inserted diagonals form the next round's list.
+__device__ void apply_spill_requests(const DevGraph &g, const Slab<true> &s, Sh &sh, uint32_t n_req,
+                                     int next_par, LEnt *next_list, uint32_t *next_count) {
     const uint32_t nr = min(n_req, s.cap);
     for (uint32_t r = threadIdx.x; r < nr; r += blockDim.x) {
-        const int4 q = __ldcg(&s.req[r]);
-        spill_arcs<true>(g, s, sh, (uint32_t)q.x, q.y, (uint32_t)q.w, (uint32_t)q.z, stamp, par,
-                         next_list, next_count);
+        const int4 rq = __ldcg(&s.req[r]);
+        const int ku = rq.x;
+        const long long cand = pk(0, kTagPend, (uint32_t)rq.y);
+        for (uint32_t a = (uint32_t)rq.z; a < (uint32_t)rq.w; ++a) {
+            const uint32_t u = __ldg(&g.arc_dst[a]);
+            const int su = find_or_insert(s, sh, tile_key(u, ku >> 3));
+            if (su < 0) return;
+            const long long prev = atomicMax(&s.slots[su].vals[ku & 7], cand);
+            if (prev < 0) {
+                atomicAdd(&sh.visited, 1ull);
+                atomicAdd(&sh.spills, 1ull);
+                reg_append(&s.slots[su].reg[next_par], next_list, next_count, s.cap, (uint32_t)su, u, ku >> 3,
+                           1u << (ku & 7), sh);
+            }
+        }
     }
 }
 
-// GwfExpand (Alg. 3) over the extended frontier, with GwfPrune (Alg. 4) applied
-// to the sources on the way in.
+// Offer value `cand` to lane `ln` of tile (slot, v, kb): GwfExpand's max-merge
+// into H~; the lane joins the next Q if its offset strictly improved.
 template <bool P>
-__device__ void expand_all(const DevGraph &g, const Slab<P> &s, Sh &sh, const QCtx &q,
-                           uint32_t n_e, bool prune_on, long long amax, int max_lag,
-                           uint32_t stamp, int par, uint32_t *qcount) {
+__device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, uint32_t v, int kb,
+                                      int ln, typename VT<P>::T cand, int par, uint32_t *qcount) {
+    const typename VT<P>::T prev = atomicMax(&s.slots[slot].vals[ln], cand);
+    if (prev < 0) atomicAdd(&sh.visited, 1ull);
+    if (pj(prev) < pj(cand)) reg_append(&s.slots[slot].reg[par], s.qlist, qcount, s.cap, slot, v, kb, 1u << ln, sh);
+}
+
+// GwfExpand (Alg. 3) over the extended frontier, with GwfPrune (Alg. 4) applied
+// to the sources on the way in.  Two snapshot entries per group and iteration:
+// their candidate max-merges are issued together before either registration.
+template <bool P>
+__device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e, bool prune_on,
+                           long long amax, int max_lag, int par, uint32_t *qcount) {
     using T = typename VT<P>::T;
     const int gid = threadIdx.x >> 3, ln = threadIdx.x & 7, ngroups = blockDim.x >> 3;
     const uint32_t ne = min(n_e, s.cap);
     // warp-uniform trip count: every lane of a warp reaches the shuffles together
-    for (uint32_t base = 0; base < ne; base += ngroups) {
-        const uint32_t e = base + gid;
-        const bool valid = e < ne;
-        uint32_t slot = 0, m = 0, v = 0, lv = 0;
-        int kb = 0;
-        T val = (T)-1;
-        if (valid) {
-            slot = __ldcg(&s.eslot[e]);
-            m = __ldcg(&s.emask[e]);
-            val = __ldcg(&s.evals[e * kTile + ln]);
-            const unsigned long long key = __ldcg(&s.keys[slot]);
-            v = (uint32_t)(key >> 32);
-            kb = (int)(uint32_t)key;
-            lv = __ldg(&g.vlen[v]);
-        }
-        bool act = valid && ((m >> ln) & 1u);
-        const int k = kb * kTile + ln;
-        const int j = act ? pj(val) : 0;
-        const int i = k + j;
-        const uint32_t b = pbase(val);
-        if (P && act && prune_on) {
-            const long long a = (long long)i + (long long)b + j;
-            if (amax - a >= (long long)max_lag) {
-                act = false;
-                atomicAdd(&sh.pruned, 1ull);
+    for (uint32_t base = 0; base < ne; base += 2 * ngroups) {
+        bool valid[2], ins[2], del[2];
+        EHdr h[2];
+        T c_ins[2], c_del[2], cand[2], prev[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t e = base + u * ngroups + gid;
+            valid[u] = e < ne;
+            h[u] = EHdr{0u, 0u, 0, 0u};
+            T val = (T)-1;
+            if (valid[u]) {
+                h[u] = ld_ehdr(&s.elist[e].hdr);
+                val = __ldcg(&s.elist[e].vals[ln]);
             }
+            const uint32_t m = h[u].slot_mask >> 24;
+            bool act = valid[u] && ((m >> ln) & 1u);
+            const int k = h[u].kb * kTile + ln;
+            const int j = act ? pj(val) : 0;
+            const int i = k + j;
+            const uint32_t b = pbase(val);
+            if (P && act && prune_on) {
+                const long long a = (long long)i + (long long)b + j;
+                if (amax - a >= (long long)max_lag) {
+                    act = false;
+                    atomicAdd(&sh.pruned, 1ull);
+                }
+            }
+            ins[u] = act && i < q.n;                 // (k+1, j)
+            del[u] = act && j < (int)h[u].lv;        // (k-1, j+1)
+            const bool mis = ins[u] && j < (int)h[u].lv;   // (k, j+1)
+            T c_mis;
+            if constexpr (P) {
+                c_ins[u] = ins[u] ? pk(j, kTagFresh, b) : -1ll;
+                c_del[u] = del[u] ? pk(j + 1, kTagFresh, b) : -1ll;
+                c_mis = mis ? pk(j + 1, kTagFresh, b) : -1ll;
+            } else {
+                c_ins[u] = ins[u] ? j : -1;
+                c_del[u] = del[u] ? j + 1 : -1;
+                c_mis = mis ? j + 1 : -1;
+            }
+            T from_left = __shfl_up_sync(0xFFFFFFFFu, c_ins[u], 1, 8);
+            T from_right = __shfl_down_sync(0xFFFFFFFFu, c_del[u], 1, 8);
+            if (ln == 0) from_left = (T)-1;
+            if (ln == 7) from_right = (T)-1;
+            cand[u] = c_mis;
+            if (from_left > cand[u]) cand[u] = from_left;
+            if (from_right > cand[u]) cand[u] = from_right;
         }
-        const bool ins = act && i < q.n;            // (k+1, j)
-        const bool del = act && j < (int)lv;        // (k-1, j+1)
-        const bool mis = ins && j < (int)lv;        // (k, j+1)
-        T c_ins, c_del, c_mis;
-        if constexpr (P) {
-            c_ins = ins ? pk(j, kTagFresh, b) : -1ll;
-            c_del = del ? pk(j + 1, kTagFresh, b) : -1ll;
-            c_mis = mis ? pk(j + 1, kTagFresh, b) : -1ll;
-        } else {
-            c_ins = ins ? j : -1;
-            c_del = del ? j + 1 : -1;
-            c_mis = mis ? j + 1 : -1;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            prev[u] = (T)0x7FFFFFFF;
+            if (valid[u] && cand[u] >= 0)
+                prev[u] = atomicMax(&s.slots[h[u].slot_mask & 0xFFFFFFu].vals[ln], cand[u]);
         }
-        T from_left = __shfl_up_sync(0xFFFFFFFFu, c_ins, 1, 8);
-        T from_right = __shfl_down_sync(0xFFFFFFFFu, c_del, 1, 8);
-        if (ln == 0) from_left = (T)-1;
-        if (ln == 7) from_right = (T)-1;
-        T cand = c_mis;
-        if (from_left > cand) cand = from_left;
-        if (from_right > cand) cand = from_right;
-        if (valid && cand >= 0) offer<P>(s, sh, (int)slot, ln, cand, stamp, par, qcount);
-        if (valid && ln == 7 && ins) {   // insertion leaves the tile: (v, 8(kb+1))
-            const int t = find_or_insert(s, sh, tile_key(v, kb + 1));
-            if (t >= 0) offer<P>(s, sh, t, 0, c_ins, stamp, par, qcount);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!(valid[u] && cand[u] >= 0)) continue;
+            if (prev[u] < 0) atomicAdd(&sh.visited, 1ull);
+            if (pj(prev[u]) < pj(cand[u]))
+                reg_append(&s.slots[h[u].slot_mask & 0xFFFFFFu].reg[par], s.qlist, qcount, s.cap,
+                           h[u].slot_mask & 0xFFFFFFu, h[u].v,
+                           h[u].kb, 1u << ln, sh);
         }
-        if (valid && ln == 0 && del) {   // deletion leaves the tile: (v, 8 kb - 1)
-            const int t = find_or_insert(s, sh, tile_key(v, kb - 1));
-            if (t >= 0) offer<P>(s, sh, t, 7, c_del, stamp, par, qcount);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (valid[u] && ln == 7 && ins[u]) {   // insertion leaves the tile: (v, 8(kb+1))
+                const int t = find_or_insert(s, sh, tile_key(h[u].v, h[u].kb + 1));
+                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb + 1, 0, c_ins[u], par, qcount);
+            }
+            if (valid[u] && ln == 0 && del[u]) {   // deletion leaves the tile: (v, 8 kb - 1)
+                const int t = find_or_insert(s, sh, tile_key(h[u].v, h[u].kb - 1));
+                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb - 1, 7, c_del[u], par, qcount);
+            }
         }
     }
 }
@@ -388,11 +520,10 @@ __device__ void wipe_touched(const Slab<P> &s, uint32_t nt) {
     nt = min(nt, s.cap);
     for (uint32_t t = threadIdx.x; t < nt * kTile; t += blockDim.x) {
         const uint32_t slot = __ldcg(&s.touched[t / kTile]);
-        __stcg(&s.vals[slot * kTile + (t % kTile)], (T)-1);
+        __stcg(&s.slots[slot].vals[t % kTile], (T)-1);
         if (t % kTile == 0) {
-            __stcg(&s.keys[slot], kEmptyKey);
-            __stcg(&s.reg[0][slot], ~0ull);
-            __stcg(&s.reg[1][slot], ~0ull);
+            __stcg(&s.slots[slot].key, kEmptyKey);
+            __stcg((unsigned long long *)s.slots[slot].reg, 0ull);
         }
     }
 }
@@ -419,8 +550,8 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         }
         return;
     }
-    q.lve = __ldg(&g.vlen[q.ve]);
-    q.ke = n - (int)q.lve;
+    q.ke = n - (int)__ldg(&g.vinfo[q.ve]).y;
+    const unsigned long long t_start = globaltimer_ns();
 
     // Alg. 1 initialisation: H~_{v_s,0} <- 0, Q <- [(v_s, 0)], d <- 0
     if (threadIdx.x == 0) {
@@ -434,21 +565,22 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             typename VT<P>::T v0;
             if constexpr (P) v0 = pk(0, kTagFresh, 0);
             else v0 = 0;
-            s.vals[(uint32_t)slot * kTile] = v0;
+            s.slots[slot].vals[0] = v0;
             sh.visited = 1;
-            reg_lane(&s.reg[1][slot], 1u, 1u, sh);
-            s.qlist[0] = (uint32_t)slot;
-            sh.nq[0] = 1;
+            reg_append(&s.slots[slot].reg[1], s.qlist, &sh.nq[0], s.cap, (uint32_t)slot, vs, 0, 1u, sh);
         }
     }
     __syncthreads();
 
-    uint32_t stamp = 1;   // phase stamp of the tiles in Q
+    uint32_t phase = 1;   // parity (phase & 1) of the reg words of the tiles in Q
     int d = 0;
     int status = 0;
     int failed = 0;
+    // optional per-query statistics (thread 0): extend / expand time, rounds, tiles
+    unsigned long long st_ext = 0, st_exp = 0, st_rounds = 0, st_ext_tiles = 0, st_exp_tiles = 0,
+                       st_max_tiles = 0;
     for (;;) {
-        // ---- GwfExtend (Alg. 2), one breadth-first round per loop iteration
+        // ---- GwfExtend (Alg. 2)
         if (threadIdx.x == 0) {
             sh.ne = 0;
             sh.score_cells = 0;
@@ -459,28 +591,35 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             sh.nq[(d + 1) & 1] = 0;
         }
         __syncthreads();
-        const uint32_t *list = s.qlist;
+        const LEnt *list = s.qlist;
         uint32_t n_list = min(sh.nq[d & 1], s.cap);
-        for (int gen = 0;; ++gen) {
-            const uint32_t next_stamp = stamp + 1;
-            uint32_t *next_list = s.slist[(gen + 1) & 1];
-            // round g fills ns[(g+1)%3] and clears ns[(g+2)%3] for round g+1; the
+        const unsigned long long t_ext = A.stats ? globaltimer_ns() : 0;
+        for (int round = 0;; ++round) {
+            if (A.stats) {
+                st_rounds++;
+                st_ext_tiles += n_list;
+            }
+            const uint32_t next_phase = phase + 1;
+            LEnt *next_list = s.slist[(round + 1) & 1];
+            // round r fills ns[(r+1)%3] and clears ns[(r+2)%3] for round r+1; the
             // cleared counter was last read before the previous round's barrier
-            uint32_t *next_count = &sh.ns[(gen + 1) % 3];
-            if (threadIdx.x == 0) sh.ns[(gen + 2) % 3] = 0;
-            extend_round<P>(g, s, sh, q, list, n_list, stamp & 1, next_stamp, next_stamp & 1,
-                            next_list, next_count, &sh.nreq[gen & 1]);
+            uint32_t *next_count = &sh.ns[(round + 1) % 3];
+            if (threadIdx.x == 0) sh.ns[(round + 2) % 3] = 0;
             if constexpr (P) {
+                extend_round_prune(g, s, sh, q, list, n_list, phase & 1, &sh.nreq[round & 1]);
                 __syncthreads();
-                if (threadIdx.x == 0) sh.nreq[(gen + 1) & 1] = 0;
-                apply_spill_requests(g, s, sh, sh.nreq[gen & 1], next_stamp, next_stamp & 1,
-                                     next_list, next_count);
+                if (threadIdx.x == 0) sh.nreq[(round + 1) & 1] = 0;
+                apply_spill_requests(g, s, sh, sh.nreq[round & 1], next_phase & 1, next_list,
+                                     next_count);
+            } else {
+                extend_round_exact(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
+                                   next_count);
             }
             // every exit decision comes from a barrier reduction: sh.err may be set by
             // threads that already run the next phase, so it is never re-read for control
             failed = __syncthreads_or(sh.err != 0);
             const uint32_t ns = *next_count;
-            stamp = next_stamp;
+            phase = next_phase;
             if (failed || ns == 0) break;
             list = next_list;
             n_list = min(ns, s.cap);
@@ -488,6 +627,13 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         if (threadIdx.x == 0) {
             sh.cells += sh.score_cells;
             sh.peak = max(sh.peak, sh.score_cells);
+        }
+        unsigned long long t_exp = 0;
+        if (A.stats) {
+            t_exp = globaltimer_ns();
+            st_ext += t_exp - t_ext;
+            st_exp_tiles += sh.ne;
+            st_max_tiles = max(st_max_tiles, (unsigned long long)sh.ne);
         }
         if (failed) break;
         // end test of Alg. 1
@@ -497,16 +643,15 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         // ---- GwfPrune (Alg. 4) folded into the sources of GwfExpand (Alg. 3)
         const long long amax = (long long)sh.amax;
         const bool prune_on = P && A.max_lag > 0 && amax > (long long)A.max_lag;
-        stamp = stamp + 1;
-        expand_all<P>(g, s, sh, q, sh.ne, prune_on, amax, A.max_lag, stamp, stamp & 1,
-                      &sh.nq[d & 1]);
+        phase = phase + 1;
+        expand_all<P>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1]);
         failed = __syncthreads_or(sh.err != 0);
+        if (A.stats) st_exp += globaltimer_ns() - t_exp;
         if (failed) break;
         if (sh.nq[d & 1] == 0) {
             status = P && A.max_lag > 0 ? GWFA_ERR_EMPTY_FRONTIER : GWFA_ERR_UNREACHABLE;
             break;
         }
-        if (stamp > 0xF0000000u) { status = GWFA_ERR_CAPACITY; break; }
     }
     __syncthreads();
     if (failed) status = sh.err;   // stable now: every thread has left the processing phases
@@ -526,7 +671,19 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             r.peak_frontier = sh.peak;
             r.pruned = sh.pruned;
             r.spills = sh.spills;
+            r.device_us = (uint32_t)min((globaltimer_ns() - t_start) / 1000ull, 0xFFFFFFFFull);
             A.out[qid] = r;
+            if (A.stats) {
+                unsigned long long *o = A.stats + (uint64_t)qid * kStatWords;
+                o[0] = st_ext;
+                o[1] = st_exp;
+                o[2] = st_rounds;
+                o[3] = st_ext_tiles;
+                o[4] = st_exp_tiles;
+                o[5] = st_max_tiles;
+                o[6] = sh.nt;
+                o[7] = (unsigned long long)(d + 1);
+            }
         }
     }
     wipe_touched<P>(s, nt);
@@ -534,14 +691,14 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
 }
 
 template <bool P>
-__global__ void __launch_bounds__(512) align_kernel(TierArgs A) {
+__global__ void __launch_bounds__(512, 4) align_kernel(TierArgs A) {
     __shared__ Sh sh;
     const Slab<P> s = carve<P>(A.slabs + (uint64_t)blockIdx.x * A.slab_bytes, A.log2cap);
     const uint32_t count = A.list_count ? *A.list_count : A.count_val;
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t t = atomicAdd(A.head, 1u);
-            sh.qid = t < count ? (A.list ? A.list[t] : t) : 0xFFFFFFFFu;
+            sh.qid = t < count ? (A.list ? A.list[A.list_offset + t] : A.list_offset + t) : 0xFFFFFFFFu;
         }
         __syncthreads();
         const uint32_t qid = sh.qid;
@@ -594,6 +751,19 @@ __global__ void fill_kernel(uint4 *p, uint64_t n16) {
         p[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
 }
 
+// Slabs start empty: slot keys and offsets all ones (empty / absent), lane-mask
+// words 0 (the second 8 bytes of every slot); the lists need no initial value.
+__global__ void slab_init_kernel(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_slabs,
+                                 uint64_t slots_bytes, uint64_t slot_bytes) {
+    const uint64_t per = slab_bytes / 16, total = per * n_slabs;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t o = (i % per) * 16;
+        const bool head = o < slots_bytes && o % slot_bytes == 0;
+        ((uint4 *)slabs)[i] = head ? make_uint4(~0u, ~0u, 0u, 0u) : make_uint4(~0u, ~0u, ~0u, ~0u);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_align(const TierArgs &a, bool prune, uint32_t ctas, uint32_t threads,
@@ -618,6 +788,18 @@ cudaError_t launch_fill(void *p, uint64_t bytes, cudaStream_t st) {
     uint64_t blocks = (n16 + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     fill_kernel<<<(unsigned)blocks, 256, 0, st>>>((uint4 *)p, n16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_init(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_slabs, uint32_t log2cap,
+                             bool prune, cudaStream_t st) {
+    const SlabLayout L = slab_layout(log2cap, prune);
+    const uint64_t n16 = slab_bytes / 16 * n_slabs;
+    if (n16 == 0) return cudaSuccess;
+    uint64_t blocks = (n16 + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    slab_init_kernel<<<(unsigned)blocks, 256, 0, st>>>(slabs, slab_bytes, n_slabs,
+                                                        L.touched - L.slots, L.slot_bytes);
     return cudaGetLastError();
 }
 

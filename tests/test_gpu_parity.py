@@ -138,7 +138,9 @@ def test_batch_order_and_tiers_do_not_change_results():
     cfg.tiers[1].log2_tiles = 13
     eng2 = gw.Engine(graph, config=cfg)
     res2 = eng2.align_batch(qs.seq, qs.off, qs.v_s, qs.v_e, order=perm)
-    assert np.array_equal(base, res2)
+    for f in gw.RESULT_DTYPE.names:
+        if f != "device_us":   # wall time, not a result
+            assert np.array_equal(base[f], res2[f]), f
 
 
 def test_capacity_error_without_retry_tier():
