@@ -99,6 +99,7 @@ struct Sh {
     unsigned long long amax;
     unsigned long long cells, visited, pruned, spills;
     uint32_t peak;
+    uint32_t claim[3];  // work counters of the phases, rotating (see align_one)
 };
 
 __device__ __forceinline__ void set_err(Sh &sh, int code) { atomicCAS(&sh.err, 0, code); }
@@ -202,6 +203,15 @@ __device__ __forceinline__ void reg_append(uint32_t *regw, LEnt *list, uint32_t 
     }
 }
 
+// Dynamic work distribution inside a phase: the group's lane 0 claims the next
+// `step` entries, so a group held up by a long exact-match run or spill chain does
+// not stall the others at the phase barrier.
+__device__ __forceinline__ uint32_t group_claim(uint32_t *ctr, uint32_t step, unsigned gmask, int ln) {
+    uint32_t e = 0;
+    if (ln == 0) e = atomicAdd(ctr, step);
+    return __shfl_sync(gmask, e, 0, 8);
+}
+
 struct QCtx {
     const uint32_t *qw;   // this query's packed words
     int n;
@@ -273,14 +283,16 @@ __device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const
 // offsets, vertex info -> first LCP window) in flight together.
 __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &sh, const QCtx &q,
                                    const LEnt *list, uint32_t n_list, int par, int next_par,
-                                   LEnt *next_list, uint32_t *next_count) {
-    const int gid = threadIdx.x >> 3, ln = threadIdx.x & 7, ngroups = blockDim.x >> 3;
+                                   LEnt *next_list, uint32_t *next_count, uint32_t *claim) {
+    const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
-    for (uint32_t e0 = gid; e0 < n_list; e0 += 2 * ngroups) {
-        const bool has1 = e0 + ngroups < n_list;   // uniform within the group
+    for (;;) {
+        const uint32_t e0 = group_claim(claim, 2u, gmask, ln);
+        if (e0 >= n_list) break;
+        const bool has1 = e0 + 1 < n_list;   // uniform within the group
         LEnt ent[2];
         ent[0] = ld_lent(&list[e0]);
-        ent[1] = has1 ? ld_lent(&list[e0 + ngroups]) : ent[0];
+        ent[1] = has1 ? ld_lent(&list[e0 + 1]) : ent[0];
         uint32_t m[2] = {0u, 0u};
         int val[2];
         uint4 vi[2];
@@ -345,10 +357,13 @@ __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &
 // never touch a diagonal that was present before the round (Alg. 2's presence
 // test) and same-round spills into one diagonal merge by the larger walk base.
 __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &sh, const QCtx &q,
-                                   const LEnt *list, uint32_t n_list, int par, uint32_t *req_count) {
-    const int gid = threadIdx.x >> 3, ln = threadIdx.x & 7, ngroups = blockDim.x >> 3;
+                                   const LEnt *list, uint32_t n_list, int par, uint32_t *req_count,
+                                   uint32_t *claim) {
+    const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
-    for (uint32_t e = gid; e < n_list; e += ngroups) {
+    for (;;) {
+        const uint32_t e = group_claim(claim, 1u, gmask, ln);
+        if (e >= n_list) break;
         const LEnt ent = ld_lent(&list[e]);
         uint32_t m = 0, eidx = 0;
         if (ln == 0) m = atomicExch(&s.slots[ent.slot].reg[par], 0u);
@@ -432,18 +447,20 @@ __device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, u
 // their candidate max-merges are issued together before either registration.
 template <bool P>
 __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e, bool prune_on,
-                           long long amax, int max_lag, int par, uint32_t *qcount) {
+                           long long amax, int max_lag, int par, uint32_t *qcount, uint32_t *claim) {
     using T = typename VT<P>::T;
-    const int gid = threadIdx.x >> 3, ln = threadIdx.x & 7, ngroups = blockDim.x >> 3;
+    const int ln = threadIdx.x & 7;
+    const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     const uint32_t ne = min(n_e, s.cap);
-    // warp-uniform trip count: every lane of a warp reaches the shuffles together
-    for (uint32_t base = 0; base < ne; base += 2 * ngroups) {
+    for (;;) {
+        const uint32_t base = group_claim(claim, 2u, gmask, ln);
+        if (base >= ne) break;
         bool valid[2], ins[2], del[2];
         EHdr h[2];
         T c_ins[2], c_del[2], cand[2], prev[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const uint32_t e = base + u * ngroups + gid;
+            const uint32_t e = base + u;
             valid[u] = e < ne;
             h[u] = EHdr{0u, 0u, 0, 0u};
             T val = (T)-1;
@@ -477,8 +494,8 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
                 c_del[u] = del[u] ? j + 1 : -1;
                 c_mis = mis ? j + 1 : -1;
             }
-            T from_left = __shfl_up_sync(0xFFFFFFFFu, c_ins[u], 1, 8);
-            T from_right = __shfl_down_sync(0xFFFFFFFFu, c_del[u], 1, 8);
+            T from_left = __shfl_up_sync(gmask, c_ins[u], 1, 8);
+            T from_right = __shfl_down_sync(gmask, c_del[u], 1, 8);
             if (ln == 0) from_left = (T)-1;
             if (ln == 7) from_right = (T)-1;
             cand[u] = c_mis;
@@ -560,6 +577,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         sh.cells = sh.visited = sh.pruned = sh.spills = 0;
         sh.peak = 0;
         sh.nq[0] = sh.nq[1] = 0;
+        sh.claim[0] = sh.claim[1] = sh.claim[2] = 0;
         const int slot = find_or_insert(s, sh, tile_key(vs, 0));
         if (slot >= 0) {
             typename VT<P>::T v0;
@@ -573,6 +591,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
     __syncthreads();
 
     uint32_t phase = 1;   // parity (phase & 1) of the reg words of the tiles in Q
+    uint32_t cstep = 0;   // processing phases so far: phase number c claims with claim[c % 3]
     int d = 0;
     int status = 0;
     int failed = 0;
@@ -604,16 +623,24 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             // round r fills ns[(r+1)%3] and clears ns[(r+2)%3] for round r+1; the
             // cleared counter was last read before the previous round's barrier
             uint32_t *next_count = &sh.ns[(round + 1) % 3];
-            if (threadIdx.x == 0) sh.ns[(round + 2) % 3] = 0;
+            // processing phase c claims with claim[c % 3] and clears the two others for
+            // the next phase; both were last used before this phase's barrier
+            if (threadIdx.x == 0) {
+                sh.ns[(round + 2) % 3] = 0;
+                sh.claim[(cstep + 1) % 3] = 0;
+                sh.claim[(cstep + 2) % 3] = 0;
+            }
+            uint32_t *claim = &sh.claim[cstep % 3];
+            ++cstep;
             if constexpr (P) {
-                extend_round_prune(g, s, sh, q, list, n_list, phase & 1, &sh.nreq[round & 1]);
+                extend_round_prune(g, s, sh, q, list, n_list, phase & 1, &sh.nreq[round & 1], claim);
                 __syncthreads();
                 if (threadIdx.x == 0) sh.nreq[(round + 1) & 1] = 0;
                 apply_spill_requests(g, s, sh, sh.nreq[round & 1], next_phase & 1, next_list,
                                      next_count);
             } else {
                 extend_round_exact(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
-                                   next_count);
+                                   next_count, claim);
             }
             // every exit decision comes from a barrier reduction: sh.err may be set by
             // threads that already run the next phase, so it is never re-read for control
@@ -644,7 +671,13 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         const long long amax = (long long)sh.amax;
         const bool prune_on = P && A.max_lag > 0 && amax > (long long)A.max_lag;
         phase = phase + 1;
-        expand_all<P>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1]);
+        if (threadIdx.x == 0) {
+            sh.claim[(cstep + 1) % 3] = 0;
+            sh.claim[(cstep + 2) % 3] = 0;
+        }
+        uint32_t *claim = &sh.claim[cstep % 3];
+        ++cstep;
+        expand_all<P>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim);
         failed = __syncthreads_or(sh.err != 0);
         if (A.stats) st_exp += globaltimer_ns() - t_exp;
         if (failed) break;
