@@ -18,8 +18,11 @@
  *     memory of the graph's GPU; the caller keeps ownership of every buffer it
  *     passes and may free or reuse it when the call returns (for *_device calls:
  *     once the work queued on `stream` has completed);
- *   - a `stream` argument is a cudaStream_t passed as void*; NULL means the
- *     library's own stream of that object;
+ *   - a `stream` argument is a cudaStream_t passed as void*.  Calls that only
+ *     enqueue device work (*_device) use exactly that stream, NULL meaning the
+ *     legacy default stream, so they are ordered after whatever produced their
+ *     inputs on it; synchronous host-buffer calls use the object's own stream
+ *     when it is NULL;
  *   - sequences are ASCII A/C/G/T, either case; anything else is rejected
  *     (GWFA_ERR_INVALID) because sequences are stored 2-bit packed.
  *   - all work runs in CUDA kernels on one GPU; there is no CPU fallback: if the
@@ -217,6 +220,70 @@ uint32_t gwfa_engine_last_launches(const gwfa_engine *e);
  * the learned cost model trains on.
  */
 int gwfa_engine_set_stats(gwfa_engine *e, uint64_t *d_stats);
+
+/* tier-0 overflows of the last batch call, per tier boundary (synchronises the engine's
+ * last stream): out[t] = queries that tier t handed to tier t+1 (t < GWFA_MAX_TIERS - 1) */
+int gwfa_engine_last_retries(gwfa_engine *e, uint32_t *out);
+
+/* ---- learned cost model (scheduling only; never changes a result) -------- */
+/*
+ * A 6 -> 32 -> 32 -> 4 MLP (ReLU; FP16 weights and activations, FP32
+ * accumulation and FP32 master weights) predicts per query, in log1p units:
+ *   0 the edit distance (scores of Alg. 1), 1 the peak |Q| after GwfExtend,
+ *   2 the diagonals that enter H~ (hash memory), 3 the cells (total work).
+ * These are the work counters of gwfa_result; the model is trained on them by
+ * the library's own forward/backward/Adam kernels.  Parameters (fp32, 1412):
+ * W1[32][6], b1[32], W2[32][32], b2[32], W3[4][32], b3[4].
+ * Raw features (computed on the device, z-scored inside the model with the
+ * normalisation set by gwfa_model_set_normalization):
+ *   0 log1p(|q|); 1 fraction of 64 evenly spaced query 16-mers that occur in no
+ *   vertex label; 2 log1p(vertices with id between v_s and v_e); 3 log1p(arcs
+ *   leaving them); 4 vertices with out-degree > 1 among them per kb of query;
+ *   5 log1p(arcs from them to an equal or lower id).
+ */
+#define GWFA_MODEL_FEATURES 6
+#define GWFA_MODEL_TARGETS 4
+#define GWFA_MODEL_PARAMS 1412
+typedef struct gwfa_model gwfa_model;
+
+/* builds the graph's feature tables (sorted 16-mers of the labels, prefix counts)
+ * on the graph's device and initialises the weights from `seed` */
+int gwfa_model_create(const gwfa_graph *g, uint64_t seed, gwfa_model **out);
+int gwfa_model_destroy(gwfa_model *m);
+int gwfa_model_set_params(gwfa_model *m, const float *h_params, uint32_t n_params);
+int gwfa_model_get_params(const gwfa_model *m, float *h_params, uint32_t n_params);
+/* feature means/stds (GWFA_MODEL_FEATURES each) and target means/stds (GWFA_MODEL_TARGETS) */
+int gwfa_model_set_normalization(gwfa_model *m, const float *h_fmean, const float *h_fstd,
+                                 const float *h_tmean, const float *h_tstd);
+/* raw features of n packed queries (layout of gwfa_pack_queries_device) into d_feat[n][6] */
+int gwfa_model_features_device(gwfa_model *m, uint32_t n, const uint32_t *d_words,
+                               const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
+                               float *d_feat, void *stream);
+/* predictions d_pred[n][4] (log1p units) from raw features */
+int gwfa_model_predict_device(gwfa_model *m, uint32_t n, const float *d_feat, float *d_pred,
+                              void *stream);
+/* gradient of the mean squared error over all n samples (targets d_target[n][4] in
+ * log1p units, compared after normalisation) at the current weights, into
+ * h_grad[1412]; *h_loss = the loss.  Synchronous. */
+int gwfa_model_gradient_device(gwfa_model *m, uint32_t n, const float *d_feat, const float *d_target,
+                               float *h_grad, float *h_loss, void *stream);
+/* `steps` Adam steps (lr, beta 0.9 / 0.999) on minibatches of `batch` samples drawn
+ * as slices of seeded permutations; h_losses[steps] (may be NULL) gets each step's
+ * minibatch loss.  Synchronous. */
+int gwfa_model_train_device(gwfa_model *m, uint32_t n, const float *d_feat, const float *d_target,
+                            uint32_t steps, uint32_t batch, float lr, uint64_t seed, float *h_losses,
+                            void *stream);
+
+/*
+ * Batch plan from predicted costs (host, no GPU): h_order gets the queries by
+ * decreasing predicted cells (longest processing time first); the queries whose
+ * predicted hash tiles exceed `tier0_tiles` are moved to the front and counted in
+ * *n_wide, so they start on the engine's wide (large-slab) CTAs instead of
+ * overflowing tier 0 and being re-run.
+ *   h_pred  n x 4 predictions (log1p units, as from gwfa_model_predict_device)
+ */
+int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, uint32_t *h_order,
+                       uint32_t *n_wide);
 
 #ifdef __cplusplus
 }

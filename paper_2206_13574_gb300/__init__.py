@@ -92,6 +92,22 @@ SIGNATURES = {
     "gwfa_engine_last_launches": ([_P], _u32),
     "gwfa_engine_set_stats": ([_P, _P], ctypes.c_int),
 }
+SIGNATURES.update({
+    "gwfa_engine_last_retries": ([_P, _P], ctypes.c_int),
+    "gwfa_model_create": ([_P, _u64, ctypes.POINTER(_P)], ctypes.c_int),
+    "gwfa_model_destroy": ([_P], ctypes.c_int),
+    "gwfa_model_set_params": ([_P, _P, _u32], ctypes.c_int),
+    "gwfa_model_get_params": ([_P, _P, _u32], ctypes.c_int),
+    "gwfa_model_set_normalization": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "gwfa_model_features_device": ([_P, _u32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "gwfa_model_predict_device": ([_P, _u32, _P, _P, _P], ctypes.c_int),
+    "gwfa_model_gradient_device": ([_P, _u32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "gwfa_model_train_device": ([_P, _u32, _P, _P, _u32, _u32, ctypes.c_float, _u64, _P, _P],
+                                ctypes.c_int),
+    "gwfa_plan_schedule": ([_u32, _P, _u64, _P, _P], ctypes.c_int),
+})
+MODEL_FEATURES, MODEL_TARGETS, MODEL_PARAMS = 6, 4, 1412
+TARGET_NAMES = ("edit_distance", "peak_frontier", "visited", "cells")
 STAT_FIELDS = ("extend_ns", "expand_ns", "rounds", "extend_tiles", "expand_tiles", "max_tiles",
                "hash_tiles", "scores")
 
@@ -213,6 +229,12 @@ class Engine:
     def last_launches(self) -> int:
         return int(load().gwfa_engine_last_launches(self.handle))
 
+    def last_retries(self) -> np.ndarray:
+        """Queries each tier handed to the next in the last batch call (synchronises)."""
+        out = np.zeros(GWFA_MAX_TIERS, dtype=np.uint32)
+        _check(load().gwfa_engine_last_retries(self.handle, out.ctypes.data), "gwfa_engine_last_retries")
+        return out
+
     def set_stats(self, d_stats: int | None):
         """Per-query statistics into device memory (8 uint64 per query id), or None to stop."""
         _check(load().gwfa_engine_set_stats(self.handle, d_stats or None), "gwfa_engine_set_stats")
@@ -299,3 +321,91 @@ class DeviceBatch:
 
     def results(self) -> np.ndarray:
         return self.out.cpu().numpy().view(RESULT_DTYPE)
+
+
+class CostModel:
+    """The learned cost model (gwfa_model_*): features, predictions and training on
+    the device; parameters are fp32 numpy arrays on the host side."""
+
+    def __init__(self, graph: Graph, seed: int = 1):
+        h = _P()
+        _check(load().gwfa_model_create(graph.handle, seed, ctypes.byref(h)), "gwfa_model_create")
+        self.handle = h
+        self.graph = graph
+        self.norm = None
+
+    def features(self, batch: "DeviceBatch", stream=None):
+        import torch
+        f = torch.empty((batch.n, MODEL_FEATURES), dtype=torch.float32, device=batch.q.device)
+        st = stream if stream is not None else torch.cuda.current_stream(batch.q.device)
+        _check(load().gwfa_model_features_device(self.handle, batch.n, batch.words.data_ptr(),
+                                                 batch.q_off.data_ptr(), batch.v_s.data_ptr(),
+                                                 batch.v_e.data_ptr(), f.data_ptr(), st.cuda_stream),
+               "gwfa_model_features_device")
+        return f
+
+    def set_normalization(self, fmean, fstd, tmean, tstd):
+        arrs = [_c(a, np.float32) for a in (fmean, fstd, tmean, tstd)]
+        _check(load().gwfa_model_set_normalization(self.handle, *[a.ctypes.data for a in arrs]),
+               "gwfa_model_set_normalization")
+        self.norm = arrs
+
+    def predict(self, feat, stream=None):
+        import torch
+        p = torch.empty((feat.shape[0], MODEL_TARGETS), dtype=torch.float32, device=feat.device)
+        st = stream if stream is not None else torch.cuda.current_stream(feat.device)
+        _check(load().gwfa_model_predict_device(self.handle, feat.shape[0], feat.data_ptr(), p.data_ptr(),
+                                                st.cuda_stream), "gwfa_model_predict_device")
+        return p
+
+    def gradient(self, feat, target):
+        import torch
+        g = np.zeros(MODEL_PARAMS, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        st = torch.cuda.current_stream(feat.device).cuda_stream
+        _check(load().gwfa_model_gradient_device(self.handle, feat.shape[0], feat.data_ptr(),
+                                                 target.data_ptr(), g.ctypes.data, loss.ctypes.data,
+                                                 st or None), "gwfa_model_gradient_device")
+        return g, float(loss[0])
+
+    def train(self, feat, target, steps: int, batch: int = 512, lr: float = 3e-3, seed: int = 7):
+        import torch
+        losses = np.zeros(steps, dtype=np.float32)
+        st = torch.cuda.current_stream(feat.device).cuda_stream
+        _check(load().gwfa_model_train_device(self.handle, feat.shape[0], feat.data_ptr(), target.data_ptr(),
+                                              steps, batch, lr, seed, losses.ctypes.data, st or None),
+               "gwfa_model_train_device")
+        return losses
+
+    @property
+    def params(self) -> np.ndarray:
+        w = np.zeros(MODEL_PARAMS, dtype=np.float32)
+        _check(load().gwfa_model_get_params(self.handle, w.ctypes.data, MODEL_PARAMS), "gwfa_model_get_params")
+        return w
+
+    @params.setter
+    def params(self, w):
+        w = _c(w, np.float32)
+        _check(load().gwfa_model_set_params(self.handle, w.ctypes.data, len(w)), "gwfa_model_set_params")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gwfa_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_schedule(pred: np.ndarray, tier0_tiles: int):
+    """(order, n_wide) from predictions (n x 4, log1p units): gwfa_plan_schedule."""
+    pred = _c(pred, np.float32)
+    n = pred.shape[0]
+    order = np.zeros(n, dtype=np.uint32)
+    nw = ctypes.c_uint32()
+    _check(load().gwfa_plan_schedule(n, pred.ctypes.data, int(tier0_tiles), order.ctypes.data,
+                                     ctypes.byref(nw)), "gwfa_plan_schedule")
+    return order, int(nw.value)

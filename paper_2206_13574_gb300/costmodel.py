@@ -1,0 +1,96 @@
+"""Learned scheduling for batched alignment: wave logs -> trained cost model -> batch plan.
+
+The network itself (features, forward, backward, Adam) runs in the library's
+kernels (gwfa_model_*); this module only moves tensors between those calls:
+
+* collect(): run a batch with the engine and keep, per query, the raw features
+  and the targets log1p(edit distance, peak |Q|, visited diagonals, cells) --
+  the work counters the alignment kernels report;
+* fit(): set the normalisation from the training set, then train on the GPU;
+* plan(): predictions -> (order, n_wide) for gwfa_align_batch[_device]: longest
+  predicted work first, predicted hash overflows straight onto the large-slab
+  (wide) CTAs.  The plain scheduler is the input order or length order, with
+  every query starting in tier 0.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import CostModel, DeviceBatch, Engine, Graph, MODEL_TARGETS
+
+FIELDS = ("edit_distance", "peak_frontier", "visited", "cells")
+
+
+def targets_of(results: np.ndarray) -> np.ndarray:
+    """log1p work counters of each query (n x 4, float32)."""
+    return np.stack([np.log1p(results[f].astype(np.float64)) for f in FIELDS], axis=1).astype(np.float32)
+
+
+def collect(model: CostModel, engine: Engine, queries, order=None):
+    """(features, targets, results) of one batch; features and targets as device tensors,
+    restricted to the queries that aligned."""
+    import torch
+    batch = DeviceBatch(queries, device=engine.graph.device, order=order)
+    batch.run(engine)
+    res = batch.results()
+    feat = model.features(batch)
+    torch.cuda.synchronize()
+    ok = np.nonzero(res["status"] == 0)[0]
+    idx = torch.from_numpy(ok.astype(np.int64)).to(feat.device)
+    tgt = torch.from_numpy(targets_of(res[ok])).to(feat.device)
+    return feat.index_select(0, idx).contiguous(), tgt, res
+
+
+def fit(model: CostModel, feat, target, steps: int = 1500, batch: int = 512, lr: float = 3e-3,
+        seed: int = 7):
+    """Normalise from the training set, then train; returns the per-step losses."""
+    f = feat.double()
+    t = target.double()
+    fmean = f.mean(0).cpu().numpy()
+    fstd = f.std(0).clamp_min(1e-3).cpu().numpy()
+    tmean = t.mean(0).cpu().numpy()
+    tstd = t.std(0).clamp_min(1e-3).cpu().numpy()
+    model.set_normalization(fmean, fstd, tmean, tstd)
+    return model.train(feat, target, steps=steps, batch=batch, lr=lr, seed=seed)
+
+
+def r2(pred: np.ndarray, target: np.ndarray) -> np.ndarray:
+    """Coefficient of determination per target column."""
+    ss_res = ((pred - target) ** 2).sum(0)
+    ss_tot = ((target - target.mean(0)) ** 2).sum(0)
+    return 1.0 - ss_res / np.maximum(ss_tot, 1e-12)
+
+
+def transfer(src: CostModel, dst: CostModel):
+    """Copy weights and normalisation (they do not depend on the graph)."""
+    dst.params = src.params
+    dst.set_normalization(*src.norm)
+
+
+def save(model: CostModel, path: str):
+    np.savez(path, params=model.params, fmean=model.norm[0], fstd=model.norm[1],
+             tmean=model.norm[2], tstd=model.norm[3])
+
+
+def load_into(model: CostModel, path: str):
+    z = np.load(path)
+    model.params = z["params"]
+    model.set_normalization(z["fmean"], z["fstd"], z["tmean"], z["tstd"])
+
+
+def plan(model: CostModel, batch: DeviceBatch, engine: Engine):
+    """(order, n_wide) for `batch` from the model's predictions."""
+    from . import plan_schedule
+    pred = model.predict(model.features(batch)).cpu().numpy()
+    tier0 = int(0.75 * (1 << engine.config.tiers[0].log2_tiles))
+    return plan_schedule(pred, tier0)
+
+
+def spearman(a: np.ndarray, b: np.ndarray) -> float:
+    ra = np.argsort(np.argsort(a)).astype(np.float64)
+    rb = np.argsort(np.argsort(b)).astype(np.float64)
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+__all__ = ["collect", "fit", "plan", "r2", "save", "load_into", "transfer", "targets_of", "spearman",
+           "MODEL_TARGETS", "Graph"]

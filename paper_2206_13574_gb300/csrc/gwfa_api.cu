@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -409,6 +410,41 @@ uint64_t gwfa_engine_device_bytes(const gwfa_engine *e) {
 
 uint32_t gwfa_engine_last_launches(const gwfa_engine *e) { return e ? e->last_launches : 0; }
 
+int gwfa_engine_last_retries(gwfa_engine *e, uint32_t *out) {
+    if (!e || !out) return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(e->mu);
+    int st = cuda_status(cudaSetDevice(e->g->device));
+    if (!st) st = cuda_status(cudaDeviceSynchronize());
+    if (!st)
+        st = cuda_status(cudaMemcpy(out, e->counters + GWFA_MAX_TIERS, GWFA_MAX_TIERS * 4,
+                                    cudaMemcpyDeviceToHost));
+    return st;
+}
+
+int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, uint32_t *h_order,
+                       uint32_t *n_wide) {
+    if ((n && (!h_pred || !h_order)) || !n_wide) return GWFA_ERR_INVALID;
+    std::vector<uint32_t> big, small;
+    // diagonals -> hash tiles: on the benchmark graphs a claimed 8-diagonal tile
+    // holds about 6 visited diagonals; 0.25 tiles per diagonal leaves a margin of 1.5
+    const double tile_per_diag = 0.25;
+    for (uint32_t i = 0; i < n; ++i) {
+        const double tiles = std::expm1((double)h_pred[(uint64_t)i * 4 + 2]) * tile_per_diag;
+        (tiles > (double)tier0_tiles ? big : small).push_back(i);
+    }
+    auto by_cells = [&](uint32_t a, uint32_t b) {
+        const float ca = h_pred[(uint64_t)a * 4 + 3], cb = h_pred[(uint64_t)b * 4 + 3];
+        return ca != cb ? ca > cb : a < b;
+    };
+    std::sort(big.begin(), big.end(), by_cells);
+    std::sort(small.begin(), small.end(), by_cells);
+    uint32_t k = 0;
+    for (uint32_t i : big) h_order[k++] = i;
+    for (uint32_t i : small) h_order[k++] = i;
+    *n_wide = (uint32_t)big.size();
+    return GWFA_OK;
+}
+
 int gwfa_engine_set_stats(gwfa_engine *e, uint64_t *d_stats) {
     if (!e) return GWFA_ERR_INVALID;
     std::lock_guard<std::mutex> lk(e->mu);
@@ -520,8 +556,10 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
     std::lock_guard<std::mutex> lk(e->mu);
     int st = cuda_status(cudaSetDevice(e->g->device));
     if (st) return st;
-    cudaStream_t s = stream ? (cudaStream_t)stream : e->stream;
-    return run_tiers(e, n, d_words, d_q_off, d_vs, d_ve, d_order, n_wide, d_status, o, d_out, s);
+    // exactly the caller's stream (NULL = the legacy default stream), so the batch is
+    // ordered after whatever produced its inputs on that stream
+    return run_tiers(e, n, d_words, d_q_off, d_vs, d_ve, d_order, n_wide, d_status, o, d_out,
+                     (cudaStream_t)stream);
 }
 
 int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t *h_q_off,

@@ -1,0 +1,495 @@
+// gwfa_model.cu -- learned cost model for scheduling batches of alignments.
+//
+// A tiny MLP (6 -> 32 -> 32 -> 4, ReLU) predicts, per query, log1p of: the edit
+// distance (the number of scores of Alg. 1), the peak wavefront size, the
+// number of diagonals that enter H~ (hash memory) and the total work (cells).
+// It is trained on the work counters the alignment kernels report, never
+// touches the alignment arithmetic, and is only used to order and place
+// queries; a wrong prediction costs time (an overflow re-run), not accuracy.
+//
+// Numerics: FP16 weights and activations (inputs, hidden layers), FP32
+// accumulation, FP32 master weights updated by Adam.  The network is small
+// enough that one thread evaluates one sample; gradients are accumulated per
+// block in shared memory and then atomically into global memory.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "gwfa_internal.cuh"
+
+namespace {
+
+constexpr int F = GWFA_MODEL_FEATURES;   // 6
+constexpr int H = 32;
+constexpr int O = GWFA_MODEL_TARGETS;    // 4
+constexpr int NW1 = H * F, NB1 = H, NW2 = H * H, NB2 = H, NW3 = O * H, NB3 = O;
+constexpr int OW1 = 0, OB1 = OW1 + NW1, OW2 = OB1 + NB1, OB2 = OW2 + NW2, OW3 = OB2 + NB2,
+              OB3 = OW3 + NW3, NPARAM = OB3 + NB3;
+static_assert(NPARAM == GWFA_MODEL_PARAMS, "parameter count");
+constexpr int K = 16;       // k-mer length of the divergence feature
+constexpr int SAMPLES = 64; // query k-mers sampled per query
+
+// ---------------------------------------------------------------- features
+
+struct FeatGraph {
+    const uint32_t *kmers;   // sorted distinct 16-mers inside vertex labels (2-bit packed)
+    uint64_t n_kmers;
+    const uint32_t *bub;     // prefix count of vertices with out-degree > 1, nv + 1
+    const uint32_t *back;    // prefix count of arcs u -> v with v <= u, by source, nv + 1
+    const uint4 *vinfo;      // {word, len, arc_begin, arc_end} as in the alignment kernels
+    uint32_t nv;
+};
+
+__device__ __forceinline__ uint32_t qwindow16(const uint32_t *w, uint64_t p) {
+    const uint64_t wi = p >> 4;
+    const uint32_t sh = (uint32_t)(p & 15) * 2;
+    return __funnelshift_r(__ldg(w + wi), __ldg(w + wi + 1), sh);
+}
+
+__device__ bool kmer_present(const uint32_t *a, uint64_t n, uint32_t key) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint32_t x = __ldg(a + mid);
+        if (x < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < n && __ldg(a + lo) == key;
+}
+
+// Raw features of each query (one warp per query, two sampled k-mers per lane):
+//   0 log1p(|q|)
+//   1 fraction of 64 evenly spaced query 16-mers absent from the graph's labels
+//   2 log1p(vertices with id in [v_s, v_e])  -- the id interval, which is the
+//     s->e subgraph when ids follow the graph's topological order
+//   3 log1p(arcs leaving that interval's vertices)
+//   4 vertices with out-degree > 1 in the interval, per kb of query
+//   5 log1p(back arcs (to an equal or lower id) leaving the interval)
+__global__ void features_kernel(FeatGraph fg, uint32_t nq, const uint32_t *__restrict__ words,
+                                const uint64_t *__restrict__ q_off, const uint32_t *__restrict__ vs,
+                                const uint32_t *__restrict__ ve, float *__restrict__ feat) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t wpb = blockDim.x >> 5;
+    for (uint32_t qi = blockIdx.x * wpb + (threadIdx.x >> 5); qi < nq; qi += gridDim.x * wpb) {
+        const uint64_t qo = q_off[qi];
+        const uint64_t n = q_off[qi + 1] - qo;
+        const uint32_t *qw = words + (qo >> 4) + qi;
+        int miss = 0;
+        if (n >= K) {
+            for (int t = lane; t < SAMPLES; t += 32) {
+                const uint64_t p = (uint64_t)t * (n - K) / (SAMPLES - 1);
+                miss += kmer_present(fg.kmers, fg.n_kmers, qwindow16(qw, p)) ? 0 : 1;
+            }
+        }
+        for (int o = 16; o >= 1; o >>= 1) miss += __shfl_xor_sync(0xFFFFFFFFu, miss, o);
+        if (lane == 0) {
+            uint32_t a = vs[qi], b = ve[qi];
+            if (a >= fg.nv) a = fg.nv - 1;
+            if (b >= fg.nv) b = fg.nv - 1;
+            const uint32_t lo = min(a, b), hi = max(a, b);
+            const float nverts = (float)(hi - lo + 1);
+            const float narcs = (float)(fg.vinfo[hi].w - fg.vinfo[lo].z);
+            const float nbub = (float)(fg.bub[hi + 1] - fg.bub[lo]);
+            const float nback = (float)(fg.back[hi + 1] - fg.back[lo]);
+            float *f = feat + (uint64_t)qi * F;
+            f[0] = log1pf((float)n);
+            f[1] = n >= K ? (float)miss / SAMPLES : 0.f;
+            f[2] = log1pf(nverts);
+            f[3] = log1pf(narcs);
+            f[4] = nbub * 1000.f / (float)max(n, (uint64_t)1);
+            f[5] = log1pf(nback);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- MLP
+
+struct Norm {
+    float fmean[F], fstd[F], tmean[O], tstd[O];
+};
+
+// one sample forward: FP16 inputs / activations / weights, FP32 accumulation
+__device__ __forceinline__ void mlp_forward(const __half *__restrict__ w, const Norm &nm,
+                                            const float *__restrict__ f, __half xs[F], __half h1[H],
+                                            __half h2[H], float out[O]) {
+    for (int i = 0; i < F; ++i) xs[i] = __float2half((f[i] - nm.fmean[i]) / nm.fstd[i]);
+    for (int o = 0; o < H; ++o) {
+        float acc = __half2float(w[OB1 + o]);
+        for (int i = 0; i < F; ++i) acc = fmaf(__half2float(w[OW1 + o * F + i]), __half2float(xs[i]), acc);
+        h1[o] = __float2half(fmaxf(acc, 0.f));
+    }
+    for (int o = 0; o < H; ++o) {
+        float acc = __half2float(w[OB2 + o]);
+        for (int i = 0; i < H; ++i) acc = fmaf(__half2float(w[OW2 + o * H + i]), __half2float(h1[i]), acc);
+        h2[o] = __float2half(fmaxf(acc, 0.f));
+    }
+    for (int o = 0; o < O; ++o) {
+        float acc = __half2float(w[OB3 + o]);
+        for (int i = 0; i < H; ++i) acc = fmaf(__half2float(w[OW3 + o * H + i]), __half2float(h2[i]), acc);
+        out[o] = acc;   // normalised target units
+    }
+}
+
+__global__ void predict_kernel(const __half *__restrict__ w16, Norm nm, uint32_t n,
+                               const float *__restrict__ feat, float *__restrict__ pred) {
+    __shared__ __half w[NPARAM];
+    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) w[i] = w16[i];
+    __syncthreads();
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        __half xs[F], h1[H], h2[H];
+        float out[O];
+        mlp_forward(w, nm, feat + (uint64_t)s * F, xs, h1, h2, out);
+        for (int o = 0; o < O; ++o) pred[(uint64_t)s * O + o] = out[o] * nm.tstd[o] + nm.tmean[o];
+    }
+}
+
+// Forward + backward of the mean squared error over `count` samples
+// (index list `idx`, or 0..count-1 when NULL), gradient summed into g (fp32),
+// loss summed into *loss.  dL/dout = 2 (out - y) / (count * O).
+__global__ void grad_kernel(const __half *__restrict__ w16, Norm nm, uint32_t count,
+                            const uint32_t *__restrict__ idx, const float *__restrict__ feat,
+                            const float *__restrict__ target, float *__restrict__ g,
+                            float *__restrict__ loss) {
+    __shared__ __half w[NPARAM];
+    __shared__ float gs[NPARAM];
+    __shared__ float ls;
+    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) {
+        w[i] = w16[i];
+        gs[i] = 0.f;
+    }
+    if (threadIdx.x == 0) ls = 0.f;
+    __syncthreads();
+    const float scale = 2.f / ((float)count * O);
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const uint32_t s = idx ? idx[t] : t;
+        __half xs[F], h1[H], h2[H];
+        float out[O], gout[O];
+        mlp_forward(w, nm, feat + (uint64_t)s * F, xs, h1, h2, out);
+        float l = 0.f;
+        for (int o = 0; o < O; ++o) {
+            const float y = (target[(uint64_t)s * O + o] - nm.tmean[o]) / nm.tstd[o];
+            const float e = out[o] - y;
+            l += e * e;
+            gout[o] = scale * e;
+        }
+        atomicAdd(&ls, l / ((float)count * O));
+        // layer 3
+        float ga2[H];
+        for (int i = 0; i < H; ++i) ga2[i] = 0.f;
+        for (int o = 0; o < O; ++o) {
+            atomicAdd(&gs[OB3 + o], gout[o]);
+            for (int i = 0; i < H; ++i) {
+                atomicAdd(&gs[OW3 + o * H + i], gout[o] * __half2float(h2[i]));
+                ga2[i] += gout[o] * __half2float(w[OW3 + o * H + i]);
+            }
+        }
+        for (int i = 0; i < H; ++i) ga2[i] = __half2float(h2[i]) > 0.f ? ga2[i] : 0.f;
+        // layer 2
+        float ga1[H];
+        for (int i = 0; i < H; ++i) ga1[i] = 0.f;
+        for (int o = 0; o < H; ++o) {
+            if (ga2[o] == 0.f) continue;
+            atomicAdd(&gs[OB2 + o], ga2[o]);
+            for (int i = 0; i < H; ++i) {
+                atomicAdd(&gs[OW2 + o * H + i], ga2[o] * __half2float(h1[i]));
+                ga1[i] += ga2[o] * __half2float(w[OW2 + o * H + i]);
+            }
+        }
+        // layer 1
+        for (int o = 0; o < H; ++o) {
+            const float ga = __half2float(h1[o]) > 0.f ? ga1[o] : 0.f;
+            if (ga == 0.f) continue;
+            atomicAdd(&gs[OB1 + o], ga);
+            for (int i = 0; i < F; ++i) atomicAdd(&gs[OW1 + o * F + i], ga * __half2float(xs[i]));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x)
+        if (gs[i] != 0.f) atomicAdd(&g[i], gs[i]);
+    if (threadIdx.x == 0) atomicAdd(loss, ls);
+}
+
+// Adam on the FP32 master weights, then the FP16 copy used by the kernels.
+__global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            float *__restrict__ g, __half *__restrict__ w16, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPARAM) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    w16[i] = __float2half(wi);
+    g[i] = 0.f;   // ready for the next step
+}
+
+__global__ void to_half_kernel(const float *__restrict__ w, __half *__restrict__ w16, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w16[i] = __float2half(w[i]);
+}
+
+int cstat(cudaError_t e) {
+    if (e == cudaSuccess) return GWFA_OK;
+    return e == cudaErrorMemoryAllocation ? GWFA_ERR_OOM : GWFA_ERR_CUDA;
+}
+
+uint64_t splitmix(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct gwfa_model {
+    const gwfa_graph *g = nullptr;
+    FeatGraph fg{};
+    uint32_t *d_kmers = nullptr, *d_bub = nullptr, *d_back = nullptr;
+    float *d_w = nullptr, *d_m = nullptr, *d_v = nullptr, *d_g = nullptr, *d_loss = nullptr;
+    __half *d_w16 = nullptr;
+    uint32_t *d_idx = nullptr;
+    uint64_t idx_cap = 0;
+    Norm norm{};
+    uint64_t adam_t = 0;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+};
+
+extern "C" {
+
+int gwfa_model_create(const gwfa_graph *g, uint64_t seed, gwfa_model **out) {
+    if (!g || !out) return GWFA_ERR_INVALID;
+    *out = nullptr;
+    int st = cstat(cudaSetDevice(g->device));
+    if (st) return st;
+    // graph-side feature tables, from the host copy of the graph
+    std::vector<uint32_t> words(g->n_words);
+    std::vector<uint4> vinfo(g->nv);
+    if (cudaMemcpy(words.data(), g->d_words, g->n_words * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(vinfo.data(), g->d_vinfo, (uint64_t)g->nv * sizeof(uint4), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return GWFA_ERR_CUDA;
+    std::vector<uint32_t> kmers;
+    kmers.reserve(g->total);
+    for (uint32_t v = 0; v < g->nv; ++v) {
+        const uint32_t w0 = vinfo[v].x, L = vinfo[v].y;
+        for (uint32_t p = 0; p + K <= L; ++p) {
+            const uint64_t pos = (uint64_t)w0 * 16 + p, wi = pos >> 4;
+            const uint32_t sh = (uint32_t)(pos & 15) * 2;
+            const uint64_t two = (uint64_t)words[wi] | ((uint64_t)words[wi + 1] << 32);
+            kmers.push_back((uint32_t)(two >> sh));
+        }
+    }
+    std::sort(kmers.begin(), kmers.end());
+    kmers.erase(std::unique(kmers.begin(), kmers.end()), kmers.end());
+    std::vector<uint32_t> bub(g->nv + 1, 0), back(g->nv + 1, 0);
+    for (uint32_t v = 0; v < g->nv; ++v) {
+        const uint32_t deg = g->h_arc_off[v + 1] - g->h_arc_off[v];
+        uint32_t nb = 0;
+        for (uint32_t a = g->h_arc_off[v]; a < g->h_arc_off[v + 1]; ++a) nb += g->h_arc_dst[a] <= v;
+        bub[v + 1] = bub[v] + (deg > 1 ? 1 : 0);
+        back[v + 1] = back[v] + nb;
+    }
+    gwfa_model *m = new (std::nothrow) gwfa_model();
+    if (!m) return GWFA_ERR_OOM;
+    m->g = g;
+    st = cstat(cudaMalloc(&m->d_kmers, std::max<uint64_t>(kmers.size(), 1) * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_bub, (uint64_t)(g->nv + 1) * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_back, (uint64_t)(g->nv + 1) * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_w, NPARAM * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_m, NPARAM * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_v, NPARAM * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_g, NPARAM * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_loss, 64));
+    if (!st) st = cstat(cudaMalloc(&m->d_w16, NPARAM * 2));
+    if (!st) st = cstat(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+    if (!st && !kmers.empty())
+        st = cstat(cudaMemcpy(m->d_kmers, kmers.data(), kmers.size() * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cstat(cudaMemcpy(m->d_bub, bub.data(), bub.size() * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cstat(cudaMemcpy(m->d_back, back.data(), back.size() * 4, cudaMemcpyHostToDevice));
+    if (st) { gwfa_model_destroy(m); return st; }
+    m->fg = FeatGraph{m->d_kmers, kmers.size(), m->d_bub, m->d_back, g->d_vinfo, g->nv};
+    // He-style initialisation from a seeded SplitMix64 stream
+    std::vector<float> w(NPARAM, 0.f);
+    uint64_t s = seed;
+    auto uni = [&]() { return (float)((splitmix(s) >> 11) * (1.0 / 9007199254740992.0)) * 2.f - 1.f; };
+    for (int i = 0; i < NW1; ++i) w[OW1 + i] = uni() * std::sqrt(6.f / F);
+    for (int i = 0; i < NW2; ++i) w[OW2 + i] = uni() * std::sqrt(6.f / H);
+    for (int i = 0; i < NW3; ++i) w[OW3 + i] = uni() * std::sqrt(3.f / H);
+    for (int i = 0; i < F; ++i) { m->norm.fmean[i] = 0.f; m->norm.fstd[i] = 1.f; }
+    for (int i = 0; i < O; ++i) { m->norm.tmean[i] = 0.f; m->norm.tstd[i] = 1.f; }
+    st = gwfa_model_set_params(m, w.data(), NPARAM);
+    if (st) { gwfa_model_destroy(m); return st; }
+    *out = m;
+    return GWFA_OK;
+}
+
+int gwfa_model_destroy(gwfa_model *m) {
+    if (!m) return GWFA_ERR_INVALID;
+    cudaSetDevice(m->g->device);
+    cudaFree(m->d_kmers);
+    cudaFree(m->d_bub);
+    cudaFree(m->d_back);
+    cudaFree(m->d_w);
+    cudaFree(m->d_m);
+    cudaFree(m->d_v);
+    cudaFree(m->d_g);
+    cudaFree(m->d_loss);
+    cudaFree(m->d_w16);
+    cudaFree(m->d_idx);
+    if (m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+    return GWFA_OK;
+}
+
+int gwfa_model_set_params(gwfa_model *m, const float *h_params, uint32_t n_params) {
+    if (!m || !h_params || n_params != NPARAM) return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(m->mu);
+    int st = cstat(cudaSetDevice(m->g->device));
+    if (!st) st = cstat(cudaMemcpy(m->d_w, h_params, NPARAM * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cstat(cudaMemset(m->d_m, 0, NPARAM * 4));
+    if (!st) st = cstat(cudaMemset(m->d_v, 0, NPARAM * 4));
+    if (!st) st = cstat(cudaMemset(m->d_g, 0, NPARAM * 4));
+    if (!st) {
+        to_half_kernel<<<(NPARAM + 255) / 256, 256>>>(m->d_w, m->d_w16, NPARAM);
+        st = cstat(cudaGetLastError());
+    }
+    if (!st) st = cstat(cudaDeviceSynchronize());
+    m->adam_t = 0;
+    return st;
+}
+
+int gwfa_model_get_params(const gwfa_model *m, float *h_params, uint32_t n_params) {
+    if (!m || !h_params || n_params != NPARAM) return GWFA_ERR_INVALID;
+    if (cudaSetDevice(m->g->device) != cudaSuccess) return GWFA_ERR_CUDA;
+    return cstat(cudaMemcpy(h_params, m->d_w, NPARAM * 4, cudaMemcpyDeviceToHost));
+}
+
+int gwfa_model_set_normalization(gwfa_model *m, const float *fmean, const float *fstd,
+                                 const float *tmean, const float *tstd) {
+    if (!m || !fmean || !fstd || !tmean || !tstd) return GWFA_ERR_INVALID;
+    for (int i = 0; i < F; ++i)
+        if (!(fstd[i] > 0.f)) return GWFA_ERR_INVALID;
+    for (int i = 0; i < O; ++i)
+        if (!(tstd[i] > 0.f)) return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(m->mu);
+    memcpy(m->norm.fmean, fmean, sizeof(m->norm.fmean));
+    memcpy(m->norm.fstd, fstd, sizeof(m->norm.fstd));
+    memcpy(m->norm.tmean, tmean, sizeof(m->norm.tmean));
+    memcpy(m->norm.tstd, tstd, sizeof(m->norm.tstd));
+    return GWFA_OK;
+}
+
+int gwfa_model_features_device(gwfa_model *m, uint32_t n, const uint32_t *d_words,
+                               const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
+                               float *d_feat, void *stream) {
+    if (!m || !d_words || !d_q_off || !d_v_s || !d_v_e || !d_feat) return GWFA_ERR_INVALID;
+    if (n == 0) return GWFA_OK;
+    int st = cstat(cudaSetDevice(m->g->device));
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;   // NULL = the legacy default stream
+    const uint32_t blocks = std::min<uint32_t>((n + 7) / 8, 65535);
+    features_kernel<<<blocks, 256, 0, s>>>(m->fg, n, d_words, d_q_off, d_v_s, d_v_e, d_feat);
+    return cstat(cudaGetLastError());
+}
+
+int gwfa_model_predict_device(gwfa_model *m, uint32_t n, const float *d_feat, float *d_pred,
+                              void *stream) {
+    if (!m || !d_feat || !d_pred) return GWFA_ERR_INVALID;
+    if (n == 0) return GWFA_OK;
+    int st = cstat(cudaSetDevice(m->g->device));
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;   // NULL = the legacy default stream
+    const uint32_t blocks = std::min<uint32_t>((n + 255) / 256, 1024);
+    predict_kernel<<<blocks, 256, 0, s>>>(m->d_w16, m->norm, n, d_feat, d_pred);
+    return cstat(cudaGetLastError());
+}
+
+int gwfa_model_gradient_device(gwfa_model *m, uint32_t n, const float *d_feat, const float *d_target,
+                               float *h_grad, float *h_loss, void *stream) {
+    if (!m || !d_feat || !d_target || !h_grad || n == 0) return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(m->mu);
+    int st = cstat(cudaSetDevice(m->g->device));
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;   // NULL = the legacy default stream
+    st = cstat(cudaMemsetAsync(m->d_g, 0, NPARAM * 4, s));
+    if (!st) st = cstat(cudaMemsetAsync(m->d_loss, 0, 4, s));
+    if (st) return st;
+    const uint32_t blocks = std::min<uint32_t>((n + 127) / 128, 512);
+    grad_kernel<<<blocks, 128, 0, s>>>(m->d_w16, m->norm, n, nullptr, d_feat, d_target, m->d_g, m->d_loss);
+    st = cstat(cudaGetLastError());
+    if (!st) st = cstat(cudaMemcpyAsync(h_grad, m->d_g, NPARAM * 4, cudaMemcpyDeviceToHost, s));
+    if (!st && h_loss) st = cstat(cudaMemcpyAsync(h_loss, m->d_loss, 4, cudaMemcpyDeviceToHost, s));
+    if (!st) st = cstat(cudaMemsetAsync(m->d_g, 0, NPARAM * 4, s));
+    if (!st) st = cstat(cudaStreamSynchronize(s));
+    return st;
+}
+
+int gwfa_model_train_device(gwfa_model *m, uint32_t n, const float *d_feat, const float *d_target,
+                            uint32_t steps, uint32_t batch, float lr, uint64_t seed, float *h_losses,
+                            void *stream) {
+    if (!m || !d_feat || !d_target || n == 0 || steps == 0 || batch == 0 || !(lr > 0.f))
+        return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(m->mu);
+    int st = cstat(cudaSetDevice(m->g->device));
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;   // NULL = the legacy default stream
+    batch = std::min(batch, n);
+    // minibatch index lists: consecutive slices of seeded permutations, on the device
+    const uint64_t total = (uint64_t)steps * batch;
+    if (m->idx_cap < total) {
+        cudaFree(m->d_idx);
+        m->d_idx = nullptr;
+        m->idx_cap = 0;
+        st = cstat(cudaMalloc(&m->d_idx, total * 4));
+        if (st) return st;
+        m->idx_cap = total;
+    }
+    std::vector<uint32_t> perm(n), idx(total);
+    uint64_t rs = seed;
+    uint64_t k = 0;
+    while (k < total) {
+        for (uint32_t i = 0; i < n; ++i) perm[i] = i;
+        for (uint32_t i = n - 1; i > 0; --i) std::swap(perm[i], perm[splitmix(rs) % (i + 1)]);
+        for (uint32_t i = 0; i < n && k < total; ++i) idx[k++] = perm[i];
+    }
+    st = cstat(cudaMemcpyAsync(m->d_idx, idx.data(), total * 4, cudaMemcpyHostToDevice, s));
+    if (!st) st = cstat(cudaMemsetAsync(m->d_g, 0, NPARAM * 4, s));
+    if (!st) st = cstat(cudaMemsetAsync(m->d_loss, 0, 64, s));
+    if (st) return st;
+    std::vector<float> losses;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const uint32_t blocks = std::min<uint32_t>((batch + 127) / 128, 256);
+    for (uint32_t t = 0; t < steps; ++t) {
+        grad_kernel<<<blocks, 128, 0, s>>>(m->d_w16, m->norm, batch, m->d_idx + (uint64_t)t * batch,
+                                           d_feat, d_target, m->d_g, m->d_loss + (t & 7));
+        ++m->adam_t;
+        const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
+        adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(m->d_w, m->d_m, m->d_v, m->d_g, m->d_w16, lr, b1,
+                                                        b2, eps, c1, c2);
+        st = cstat(cudaGetLastError());
+        if (st) return st;
+        if (h_losses && ((t & 7) == 7 || t + 1 == steps)) {
+            float l8[8];
+            st = cstat(cudaMemcpyAsync(l8, m->d_loss, 32, cudaMemcpyDeviceToHost, s));
+            if (!st) st = cstat(cudaMemsetAsync(m->d_loss, 0, 32, s));
+            if (!st) st = cstat(cudaStreamSynchronize(s));
+            if (st) return st;
+            for (uint32_t j = t - (t & 7); j <= t; ++j) h_losses[j] = l8[j & 7];
+        }
+    }
+    return cstat(cudaStreamSynchronize(s));
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+"""Learned cost model: CPU pins of the fp64 reference and the planner; GPU parity of
+the feature, gradient and training kernels; the gain of the learned schedule."""
+import numpy as np
+import pytest
+
+import paper_2206_13574_gb300 as gw
+from oracle import mlp_ref
+from paper_2206_13574_gb300 import _build, synth
+
+K = 16
+
+
+def _codes(b: bytes) -> np.ndarray:
+    lut = np.zeros(256, dtype=np.uint64)
+    for ch, c in zip(b"ACGTacgt", [0, 1, 2, 3, 0, 1, 2, 3]):
+        lut[ch] = c
+    return lut[np.frombuffer(b, dtype=np.uint8)]
+
+
+def _kmer(codes: np.ndarray, p: int) -> int:
+    return int(sum(int(codes[p + t]) << (2 * t) for t in range(K)))
+
+
+def cpu_features(g, qs) -> np.ndarray:
+    """The six raw features, computed the plain way."""
+    kset = set()
+    for v in range(g.n_vertices):
+        c = _codes(g.label(v))
+        for p in range(len(c) - K + 1):
+            kset.add(_kmer(c, p))
+    lens = g.lengths()
+    outdeg = np.bincount(g.arc_src, minlength=g.n_vertices)
+    out = np.zeros((len(qs), 6), dtype=np.float64)
+    for i in range(len(qs)):
+        q = _codes(qs.query(i))
+        n = len(q)
+        miss = 0
+        if n >= K:
+            for t in range(64):
+                miss += _kmer(q, t * (n - K) // 63) not in kset
+        lo, hi = sorted((int(qs.v_s[i]), int(qs.v_e[i])))
+        sel = (g.arc_src >= lo) & (g.arc_src <= hi)
+        out[i] = [np.log1p(n), miss / 64 if n >= K else 0.0, np.log1p(hi - lo + 1), np.log1p(sel.sum()),
+                  (outdeg[lo:hi + 1] > 1).sum() * 1000.0 / max(n, 1),
+                  np.log1p((sel & (g.arc_dst <= g.arc_src)).sum())]
+    return out
+
+
+# ------------------------------------------------------------------ CPU pins
+
+
+def test_reference_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    w = rng.normal(0, 0.3, mlp_ref.NPARAM)
+    feat = rng.normal(0, 1, (40, 6))
+    tgt = rng.normal(0, 1, (40, 4))
+    args = (np.zeros(6), np.ones(6), np.zeros(4), np.ones(4))
+    loss, g = mlp_ref.loss_and_grad(w, feat, tgt, *args, emulate_fp16=False)
+    for i in rng.choice(mlp_ref.NPARAM, 60, replace=False):
+        e = np.zeros_like(w)
+        e[i] = 1e-6
+        lp, _ = mlp_ref.loss_and_grad(w + e, feat, tgt, *args, emulate_fp16=False)
+        lm, _ = mlp_ref.loss_and_grad(w - e, feat, tgt, *args, emulate_fp16=False)
+        fd = (lp - lm) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
+def test_plan_schedule_orders_by_predicted_work_and_routes_big():
+    _build.build()
+    pred = np.zeros((6, 4), dtype=np.float32)
+    pred[:, 3] = [3, 9, 1, 7, 5, 2]                 # log1p cells
+    pred[:, 2] = [1, 1, 1, 20, 1, 21]                # log1p visited: queries 3 and 5 are huge
+    order, n_wide = gw.plan_schedule(pred, tier0_tiles=1000)
+    assert n_wide == 2
+    assert list(order[:2]) == [3, 5]                 # big ones first, by predicted cells
+    assert list(order[2:]) == [1, 4, 0, 2]           # the rest longest-predicted-first
+    order, n_wide = gw.plan_schedule(pred, tier0_tiles=10 ** 12)
+    assert n_wide == 0 and list(order) == [1, 3, 4, 0, 5, 2]
+
+
+# ------------------------------------------------------------------ GPU
+
+
+@pytest.fixture(scope="module")
+def c2small():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    _build.build()
+    g, qs = synth.make_config(2, n_queries=600)
+    graph = gw.Graph.from_synth(g)
+    return g, qs, graph
+
+
+@pytest.mark.gpu
+def test_features_match_cpu(c2small):
+    g, qs, graph = c2small
+    sub = qs.subset(np.arange(0, 600, 10))
+    m = gw.CostModel(graph)
+    f = m.features(gw.DeviceBatch(sub)).cpu().numpy().astype(np.float64)
+    ref = cpu_features(g, sub)
+    assert np.array_equal(f[:, 1], ref[:, 1].astype(np.float32).astype(np.float64))   # k-mer misses exact
+    assert np.allclose(f, ref, rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.gpu
+def test_gradient_matches_fp64_reference(c2small):
+    import torch
+    g, qs, graph = c2small
+    m = gw.CostModel(graph, seed=3)
+    eng = gw.Engine(graph)
+    from paper_2206_13574_gb300 import costmodel
+    feat, tgt, _ = costmodel.collect(m, eng, qs.subset(np.arange(200)))
+    f = feat.double()
+    t = tgt.double()
+    norm = [f.mean(0).cpu().numpy(), f.std(0).clamp_min(1e-3).cpu().numpy(),
+            t.mean(0).cpu().numpy(), t.std(0).clamp_min(1e-3).cpu().numpy()]
+    m.set_normalization(*norm)
+    grad, loss = m.gradient(feat, tgt)
+    w16 = m.params.astype(np.float16).astype(np.float64)   # the kernels run on fp16 weights
+    rl, rg = mlp_ref.loss_and_grad(w16, feat.cpu().numpy(), tgt.cpu().numpy(),
+                                   *[np.asarray(a, np.float32).astype(np.float64) for a in norm])
+    assert abs(loss - rl) <= 2e-2 * abs(rl)
+    assert np.linalg.norm(grad - rg) <= 2e-2 * np.linalg.norm(rg)
+    big = np.abs(rg) > 1e-2 * np.abs(rg).max()
+    assert np.all(np.abs(grad[big] - rg[big]) <= 2e-2 * np.abs(rg[big]) + 1e-4 * np.abs(rg).max())
+
+
+@pytest.mark.gpu
+def test_training_learns_work_counts(c2small):
+    from paper_2206_13574_gb300 import costmodel
+    g, qs, graph = c2small
+    m = gw.CostModel(graph, seed=5)
+    eng = gw.Engine(graph)
+    feat, tgt, _ = costmodel.collect(m, eng, qs.subset(np.arange(400)))
+    losses = costmodel.fit(m, feat, tgt, steps=800, batch=256, lr=3e-3)
+    assert losses[-50:].mean() < 0.5 * losses[:20].mean()
+    tf, tt, _ = costmodel.collect(m, eng, qs.subset(np.arange(400, 600)))
+    pred = m.predict(tf).cpu().numpy()
+    r2 = costmodel.r2(pred, tt.cpu().numpy())
+    assert r2[0] > 0.6 and r2[3] > 0.6, r2         # distance and work on held-out queries
+
+
+@pytest.mark.gpu
+def test_learned_schedule_keeps_results_and_avoids_overflow_reruns(c2small):
+    """Same results under the learned plan; fewer queries overflow tier 0 and run twice."""
+    from paper_2206_13574_gb300 import costmodel
+    g, qs, graph = c2small
+    m = gw.CostModel(graph, seed=5)
+    cfg = gw.default_config(graph)
+    cfg.tiers[0].log2_tiles = 12             # small tier-0 slabs: overflow is common
+    cfg.wide.ctas = 64
+    cfg.wide.log2_tiles = 17
+    eng = gw.Engine(graph, config=cfg)
+    feat, tgt, _ = costmodel.collect(m, eng, qs.subset(np.arange(400)))
+    costmodel.fit(m, feat, tgt, steps=800, batch=256, lr=3e-3)
+    test = qs.subset(np.arange(400, 600))
+    b = gw.DeviceBatch(test)
+    b.run(eng)
+    plain = b.results()
+    plain_retries = int(eng.last_retries()[0])
+    order, n_wide = costmodel.plan(m, b, eng)
+    b2 = gw.DeviceBatch(test, order=order)
+    b2.run(eng, n_wide=n_wide)
+    learned = b2.results()
+    learned_retries = int(eng.last_retries()[0])
+    for f in ("status", "edit_distance", "cells", "visited", "peak_frontier"):
+        assert np.array_equal(plain[f], learned[f]), f
+    assert plain_retries > 0
+    assert learned_retries < plain_retries, (learned_retries, plain_retries, n_wide)
