@@ -274,6 +274,11 @@ int gwfa_model_train_device(gwfa_model *m, uint32_t n, const float *d_feat, cons
                             uint32_t steps, uint32_t batch, float lr, uint64_t seed, float *h_losses,
                             void *stream);
 
+/* the same prediction for one ASCII query, evaluated on the host in fp32 with the
+ * current weights (used for admission control in serving) */
+int gwfa_model_predict_host(const gwfa_model *m, const char *h_q, uint32_t n, uint32_t v_s,
+                            uint32_t v_e, float *h_pred);
+
 /*
  * Batch plan from predicted costs (host, no GPU): h_order gets the queries by
  * decreasing predicted cells (longest processing time first); the queries whose
@@ -284,6 +289,51 @@ int gwfa_model_train_device(gwfa_model *m, uint32_t n, const float *d_feat, cons
  */
 int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, uint32_t *h_order,
                        uint32_t *n_wide);
+
+/* ---- serving: continuous batching over a resident graph ----------------- */
+/*
+ * A persistent kernel keeps the graph resident and takes requests as its CTAs
+ * free up; requests submitted while others are on the GPU start without waiting
+ * for a batch boundary.  Requests and results pass through pinned host memory
+ * mapped into the device.  Two request classes: CTAs with small hash slabs
+ * (ctas_small, 2^log2_small tiles) and CTAs with large ones (ctas_big,
+ * 2^log2_big); a request enters the class its predicted hash memory fits (the
+ * attached cost model, else length > big_length), and a request that overflows
+ * a small slab is re-queued into the large class automatically.  The kernel's
+ * CTAs leave after idle_us without work (every device wait is bounded) and the
+ * next submit or poll starts it again.  Results are identical to gwfa_align.
+ * Thread-safe (one internal lock).
+ */
+typedef struct gwfa_server gwfa_server;
+typedef struct {
+    uint32_t threads;          /* per CTA */
+    uint32_t ctas_small, log2_small;
+    uint32_t ctas_big, log2_big;
+    uint32_t ring_slots;       /* requests in flight per class */
+    uint32_t max_query_len;    /* longer requests are rejected (GWFA_ERR_INVALID) */
+    uint32_t idle_us;          /* idle time after which the kernel's CTAs leave */
+    uint32_t big_length;       /* without a cost model: class 1 iff |q| > big_length */
+} gwfa_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, requeued, launches, in_flight, device_bytes;
+} gwfa_server_stats;
+
+int gwfa_server_default_config(const gwfa_graph *g, gwfa_server_config *cfg);
+/* `model` (may be NULL) must outlive the server */
+int gwfa_server_create(const gwfa_graph *g, const gwfa_server_config *cfg, const gwfa_opts *opts,
+                       const gwfa_model *model, gwfa_server **out);
+/* GWFA_OK with *ticket set, GWFA_PENDING when the class's ring is full (retry later),
+ * GWFA_ERR_INVALID for a bad query */
+int gwfa_submit(gwfa_server *s, const char *h_q, uint32_t n, uint32_t v_s, uint32_t v_e,
+                uint64_t *ticket);
+/* GWFA_OK with *out filled (once per ticket), or GWFA_PENDING */
+int gwfa_poll(gwfa_server *s, uint64_t ticket, gwfa_result *out);
+/* polls until done or timeout_ms (GWFA_ERR_TIMEOUT) */
+int gwfa_wait(gwfa_server *s, uint64_t ticket, uint32_t timeout_ms, gwfa_result *out);
+int gwfa_server_get_stats(gwfa_server *s, gwfa_server_stats *out);
+/* stops the kernel (requests on the GPU finish first) and frees everything */
+int gwfa_server_destroy(gwfa_server *s);
 
 #ifdef __cplusplus
 }

@@ -106,6 +106,31 @@ SIGNATURES.update({
                                 ctypes.c_int),
     "gwfa_plan_schedule": ([_u32, _P, _u64, _P, _P], ctypes.c_int),
 })
+
+
+
+class gwfa_server_config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("threads", "ctas_small", "log2_small", "ctas_big",
+                                                 "log2_big", "ring_slots", "max_query_len", "idle_us",
+                                                 "big_length")]
+
+
+class gwfa_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "requeued", "launches",
+                                                 "in_flight", "device_bytes")]
+
+
+SIGNATURES.update({
+    "gwfa_model_predict_host": ([_P, _P, _u32, _u32, _u32, _P], ctypes.c_int),
+    "gwfa_server_default_config": ([_P, ctypes.POINTER(gwfa_server_config)], ctypes.c_int),
+    "gwfa_server_create": ([_P, ctypes.POINTER(gwfa_server_config), ctypes.POINTER(gwfa_opts), _P,
+                            ctypes.POINTER(_P)], ctypes.c_int),
+    "gwfa_submit": ([_P, _P, _u32, _u32, _u32, ctypes.POINTER(_u64)], ctypes.c_int),
+    "gwfa_poll": ([_P, _u64, ctypes.POINTER(gwfa_result)], ctypes.c_int),
+    "gwfa_wait": ([_P, _u64, _u32, ctypes.POINTER(gwfa_result)], ctypes.c_int),
+    "gwfa_server_get_stats": ([_P, ctypes.POINTER(gwfa_server_stats)], ctypes.c_int),
+    "gwfa_server_destroy": ([_P], ctypes.c_int),
+})
 MODEL_FEATURES, MODEL_TARGETS, MODEL_PARAMS = 6, 4, 1412
 TARGET_NAMES = ("edit_distance", "peak_frontier", "visited", "cells")
 STAT_FIELDS = ("extend_ns", "expand_ns", "rounds", "extend_tiles", "expand_tiles", "max_tiles",
@@ -409,3 +434,62 @@ def plan_schedule(pred: np.ndarray, tier0_tiles: int):
     _check(load().gwfa_plan_schedule(n, pred.ctypes.data, int(tier0_tiles), order.ctypes.data,
                                      ctypes.byref(nw)), "gwfa_plan_schedule")
     return order, int(nw.value)
+
+
+class Server:
+    """Continuous-batching server over a resident graph (gwfa_server_*)."""
+
+    def __init__(self, graph: Graph, config: gwfa_server_config | None = None, max_lag: int = 0,
+                 max_score: int = -1, model: "CostModel | None" = None):
+        lib = load()
+        if config is None:
+            config = gwfa_server_config()
+            _check(lib.gwfa_server_default_config(graph.handle, ctypes.byref(config)),
+                   "gwfa_server_default_config")
+        self.config = config
+        self.graph = graph
+        self.model = model
+        o = _opts(max_lag, max_score)
+        h = _P()
+        _check(lib.gwfa_server_create(graph.handle, ctypes.byref(config), ctypes.byref(o),
+                                      model.handle if model is not None else None, ctypes.byref(h)),
+               "gwfa_server_create")
+        self.handle = h
+
+    def submit(self, q: bytes, v_s: int, v_e: int) -> int | None:
+        """Ticket, or None when the ring is full (retry later)."""
+        t = ctypes.c_uint64()
+        st = load().gwfa_submit(self.handle, q, len(q), v_s, v_e, ctypes.byref(t))
+        if st == GWFA_PENDING:
+            return None
+        _check(st, "gwfa_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int) -> dict | None:
+        r = gwfa_result()
+        st = load().gwfa_poll(self.handle, ticket, ctypes.byref(r))
+        if st == GWFA_PENDING:
+            return None
+        _check(st, "gwfa_poll")
+        return r.as_dict()
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        r = gwfa_result()
+        _check(load().gwfa_wait(self.handle, ticket, timeout_ms, ctypes.byref(r)), "gwfa_wait")
+        return r.as_dict()
+
+    def stats(self) -> dict:
+        s = gwfa_server_stats()
+        _check(load().gwfa_server_get_stats(self.handle, ctypes.byref(s)), "gwfa_server_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gwfa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -106,8 +106,37 @@ struct TierArgs {
     int32_t max_lag;
     int32_t max_score;
     unsigned long long *stats;  // optional, kStatWords per query id (see gwfa_engine_set_stats)
+    int q_smem;                 // query words are in shared memory (server kernel)
 };
 constexpr int kStatWords = 8;
+
+// A serving request as the host publishes it (pinned, mapped host memory).
+struct ReqDesc {
+    unsigned long long ticket;
+    uint32_t n, v_s, v_e, pad;
+    uint64_t pad2;
+};
+
+// Arguments of the persistent server kernel; the rings live in mapped host memory.
+struct ServerArgs {
+    DevGraph g;
+    uint8_t *slabs;
+    uint64_t slab_bytes[2];
+    uint64_t big_offset;           // byte offset of the class-1 slabs
+    uint32_t log2cap[2];
+    uint32_t n_small;              // CTAs serving class 0
+    const ReqDesc *desc[2];
+    const uint32_t *arena[2];      // packed query words, slot_words per ring slot
+    gwfa_result *results[2];
+    unsigned long long *done[2];   // ticket + 1 once results[slot] is final
+    const unsigned long long *tail[2];
+    unsigned long long *head;      // device, per class
+    const unsigned long long *stop;
+    unsigned long long *timeouts;  // device: CTAs that left after wait_limit idle polls
+    uint32_t ring, slot_words;
+    uint32_t wait_limit, sleep_ns;
+    int32_t max_lag, max_score;
+};
 
 // launchers (gwfa_kernels.cu)
 cudaError_t launch_align(const TierArgs &a, bool prune, uint32_t ctas, uint32_t threads,
@@ -118,6 +147,8 @@ cudaError_t launch_fill(void *p, uint64_t bytes, cudaStream_t st);
 cudaError_t launch_slab_init(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_slabs, uint32_t log2cap,
                              bool prune, cudaStream_t st);
 int align_occupancy(bool prune, uint32_t threads, int *blocks_per_sm);
+cudaError_t launch_server(const ServerArgs &a, bool prune, uint32_t ctas, uint32_t threads,
+                          uint32_t smem_bytes, cudaStream_t st);
 
 }  // namespace gwfa
 

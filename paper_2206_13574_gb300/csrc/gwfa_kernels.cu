@@ -130,14 +130,38 @@ __device__ __forceinline__ uint32_t window16(const uint32_t *__restrict__ w, uin
     return __funnelshift_r(lo, hi, sh);
 }
 
+struct QCtx {
+    const uint32_t *qw;   // this query's packed words (global, or staged in shared memory)
+    int n;
+    uint32_t ve;
+    int ke;
+    bool smem;            // qw points to shared memory (server kernel)
+};
+
+// 16 query bases from position p: read-only cache for a batch staged before the
+// launch, plain (shared-memory) loads for a query the CTA staged itself.
+__device__ __forceinline__ uint32_t qwin(const QCtx &q, uint64_t p) {
+    const uint64_t wi = p >> 4;
+    const uint32_t sh = (uint32_t)(p & 15) * 2;
+    uint32_t lo, hi;
+    if (q.smem) {
+        lo = q.qw[wi];
+        hi = q.qw[wi + 1];
+    } else {
+        lo = __ldg(q.qw + wi);
+        hi = __ldg(q.qw + wi + 1);
+    }
+    return __funnelshift_r(lo, hi, sh);
+}
+
 // LCP(q[i+1..|q|], v[j+1..|v|]) of Eq. 2 in 0-based positions: XOR of 16-base
 // windows, the first differing base is the lowest set bit pair.
-__device__ __forceinline__ int lcp(const uint32_t *__restrict__ qw, int i, int n,
-                                   const uint32_t *__restrict__ vw, int j, int lv) {
-    const int maxl = min(n - i, lv - j);
+__device__ __forceinline__ int lcp(const QCtx &q, int i, const uint32_t *__restrict__ vw, int j,
+                                   int lv) {
+    const int maxl = min(q.n - i, lv - j);
     int l = 0;
     while (l < maxl) {
-        const uint32_t x = window16(qw, (uint64_t)(i + l)) ^ window16(vw, (uint64_t)(j + l));
+        const uint32_t x = qwin(q, (uint64_t)(i + l)) ^ window16(vw, (uint64_t)(j + l));
         if (x) {
             l += (__ffs(x) - 1) >> 1;
             break;
@@ -149,9 +173,8 @@ __device__ __forceinline__ int lcp(const uint32_t *__restrict__ qw, int i, int n
 
 // The same LCP when the first window XOR `x` (bases i.. against j..) is already
 // loaded, so that two diagonals can have their first windows in flight together.
-__device__ __forceinline__ int lcp_finish(const uint32_t *__restrict__ qw, int i,
-                                          const uint32_t *__restrict__ vw, int j, int maxl,
-                                          uint32_t x) {
+__device__ __forceinline__ int lcp_finish(const QCtx &q, int i, const uint32_t *__restrict__ vw,
+                                          int j, int maxl, uint32_t x) {
     int l = 0;
     while (l < maxl) {
         if (x) {
@@ -160,7 +183,7 @@ __device__ __forceinline__ int lcp_finish(const uint32_t *__restrict__ qw, int i
         }
         l += 16;
         if (l >= maxl) break;
-        x = window16(qw, (uint64_t)(i + l)) ^ window16(vw, (uint64_t)(j + l));
+        x = qwin(q, (uint64_t)(i + l)) ^ window16(vw, (uint64_t)(j + l));
     }
     return min(l, maxl);
 }
@@ -212,12 +235,7 @@ __device__ __forceinline__ uint32_t group_claim(uint32_t *ctr, uint32_t step, un
     return __shfl_sync(gmask, e, 0, 8);
 }
 
-struct QCtx {
-    const uint32_t *qw;   // this query's packed words
-    int n;
-    uint32_t ve;
-    int ke;
-};
+
 
 // Exact mode: diagonal (v, k) reached |v| (Alg. 2 arc loop).  Offset 0 goes to
 // (u, k + |v|) for every arc (v, u) where it is absent; a diagonal this thread
@@ -257,7 +275,7 @@ __device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const
         const uint32_t su = st_slot[top], u = st_u[top];
         const int k = st_k[top];
         const uint4 vi = __ldg(&g.vinfo[u]);
-        const int l = lcp(q.qw, k, q.n, g.words + vi.x, 0, (int)vi.y);
+        const int l = lcp(q, k, g.words + vi.x, 0, (int)vi.y);
         __stcg(&s.slots[su].vals[k & 7], l);
         const uint32_t eidx = atomicAdd(&sh.ne, 1u);
         atomicAdd(&sh.score_cells, 1u);
@@ -323,14 +341,14 @@ __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &
                 const int i = k[u] + val[u];
                 maxl[u] = min(q.n - i, (int)vi[u].y - val[u]);
                 if (maxl[u] > 0)
-                    x[u] = window16(q.qw, (uint64_t)i) ^ window16(g.words + vi[u].x, (uint64_t)val[u]);
+                    x[u] = qwin(q, (uint64_t)i) ^ window16(g.words + vi[u].x, (uint64_t)val[u]);
             }
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             if (u == 1 && !has1) break;
             if (live[u]) {
-                val[u] += lcp_finish(q.qw, k[u] + val[u], g.words + vi[u].x, val[u], maxl[u], x[u]);
+                val[u] += lcp_finish(q, k[u] + val[u], g.words + vi[u].x, val[u], maxl[u], x[u]);
                 __stcg(&s.slots[ent[u].slot].vals[ln], val[u]);
                 if (ent[u].v == q.ve && k[u] == q.ke && (uint32_t)val[u] == vi[u].y) sh.found = 1;
             }
@@ -381,7 +399,7 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
         if (live) {
             const int j = pj(val);
             const int i = k + j;
-            const int j2 = j + lcp(q.qw, i, q.n, g.words + vi.x, j, (int)vi.y);
+            const int j2 = j + lcp(q, i, g.words + vi.x, j, (int)vi.y);
             val = pk(j2, kTagSettled, pbase(val));
             __stcg(&s.slots[ent.slot].vals[ln], val);
             if (ent.v == q.ve && k == q.ke && (uint32_t)j2 == vi.y) sh.found = 1;
@@ -553,6 +571,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
     QCtx q;
     q.qw = A.qwords + (qo >> 4) + qid;
     q.n = n;
+    q.smem = A.q_smem != 0;
     const uint32_t vs = A.v_s[qid];
     q.ve = A.v_e[qid];
     int pre = 0;
@@ -741,6 +760,91 @@ __global__ void __launch_bounds__(512, 4) align_kernel(TierArgs A) {
     }
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Serving: a persistent kernel whose CTAs take requests from host-published rings
+// (continuous batching: a CTA starts a new request as soon as it finishes one).
+// CTAs [0, n_small) serve class 0 (small hash slabs), the rest class 1.  Every
+// wait is bounded: a CTA that finds no request for wait_limit polls (or sees the
+// stop flag) leaves the loop, and the host relaunches the kernel when work comes.
+template <bool P>
+__global__ void __launch_bounds__(512, 2) server_kernel(ServerArgs S) {
+    extern __shared__ uint32_t qsm[];   // the request's packed words, staged
+    __shared__ Sh sh;
+    __shared__ unsigned long long s_ticket;
+    __shared__ uint64_t s_qoff[2];
+    __shared__ uint32_t s_vs, s_ve;
+    __shared__ int s_go;
+    const int cls = blockIdx.x < S.n_small ? 0 : 1;
+    uint8_t *base = cls == 0 ? S.slabs + (uint64_t)blockIdx.x * S.slab_bytes[0]
+                             : S.slabs + S.big_offset + (uint64_t)(blockIdx.x - S.n_small) * S.slab_bytes[1];
+    const Slab<P> s = carve<P>(base, S.log2cap[cls]);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int go = 0;
+            uint32_t polls = 0;
+            for (;;) {
+                if (ld_acquire_sys(S.stop)) break;
+                const unsigned long long h = atomicAdd(S.head + cls, 0ull);
+                const unsigned long long t = ld_acquire_sys(S.tail[cls]);
+                if (h < t) {
+                    if (atomicCAS(S.head + cls, h, h + 1) == h) {
+                        s_ticket = h;
+                        go = 1;
+                        break;
+                    }
+                    continue;
+                }
+                if (++polls > S.wait_limit) {
+                    atomicAdd(S.timeouts, 1ull);
+                    break;
+                }
+                __nanosleep(S.sleep_ns);
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const unsigned long long ticket = s_ticket;
+        const uint32_t slot = (uint32_t)(ticket % S.ring);
+        const ReqDesc *d = S.desc[cls] + slot;
+        const uint32_t n = __ldcv(&d->n);
+        const uint32_t nw = (n + 15) >> 4;
+        const uint32_t *src = S.arena[cls] + (uint64_t)slot * S.slot_words;
+        for (uint32_t w = threadIdx.x; w < nw + 2; w += blockDim.x) qsm[w] = w < nw ? __ldcv(src + w) : 0u;
+        if (threadIdx.x == 0) {
+            s_qoff[0] = 0;
+            s_qoff[1] = n;
+            s_vs = __ldcv(&d->v_s);
+            s_ve = __ldcv(&d->v_e);
+        }
+        __syncthreads();
+        TierArgs A{};
+        A.g = S.g;
+        A.qwords = qsm;
+        A.q_smem = 1;
+        A.q_off = s_qoff;
+        A.v_s = &s_vs;
+        A.v_e = &s_ve;
+        A.out = S.results[cls] + slot;
+        A.max_lag = S.max_lag;
+        A.max_score = S.max_score;
+        align_one<P>(A, s, sh, 0);
+        if (threadIdx.x == 0) {
+            __threadfence_system();
+            st_release_sys(S.done[cls] + slot, ticket + 1);
+        }
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ int base_code(unsigned char c) {
     switch (c) {
     case 'A': case 'a': return 0;
@@ -803,6 +907,18 @@ cudaError_t launch_align(const TierArgs &a, bool prune, uint32_t ctas, uint32_t 
                          cudaStream_t st) {
     if (prune) align_kernel<true><<<ctas, threads, 0, st>>>(a);
     else align_kernel<false><<<ctas, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_server(const ServerArgs &a, bool prune, uint32_t ctas, uint32_t threads,
+                          uint32_t smem_bytes, cudaStream_t st) {
+    if (prune) {
+        cudaFuncSetAttribute(server_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        server_kernel<true><<<ctas, threads, smem_bytes, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(server_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        server_kernel<false><<<ctas, threads, smem_bytes, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -254,6 +254,9 @@ uint64_t splitmix(uint64_t &s) {
 
 struct gwfa_model {
     const gwfa_graph *g = nullptr;
+    // host copies for predicting single requests on the host (serving admission)
+    std::vector<uint32_t> h_kmers, h_bub, h_back;
+    std::vector<float> h_w;
     FeatGraph fg{};
     uint32_t *d_kmers = nullptr, *d_bub = nullptr, *d_back = nullptr;
     float *d_w = nullptr, *d_m = nullptr, *d_v = nullptr, *d_g = nullptr, *d_loss = nullptr;
@@ -320,6 +323,9 @@ int gwfa_model_create(const gwfa_graph *g, uint64_t seed, gwfa_model **out) {
     if (!st) st = cstat(cudaMemcpy(m->d_back, back.data(), back.size() * 4, cudaMemcpyHostToDevice));
     if (st) { gwfa_model_destroy(m); return st; }
     m->fg = FeatGraph{m->d_kmers, kmers.size(), m->d_bub, m->d_back, g->d_vinfo, g->nv};
+    m->h_kmers = std::move(kmers);
+    m->h_bub = std::move(bub);
+    m->h_back = std::move(back);
     // He-style initialisation from a seeded SplitMix64 stream
     std::vector<float> w(NPARAM, 0.f);
     uint64_t s = seed;
@@ -367,6 +373,7 @@ int gwfa_model_set_params(gwfa_model *m, const float *h_params, uint32_t n_param
     }
     if (!st) st = cstat(cudaDeviceSynchronize());
     m->adam_t = 0;
+    if (!st) m->h_w.assign(h_params, h_params + NPARAM);
     return st;
 }
 
@@ -489,7 +496,59 @@ int gwfa_model_train_device(gwfa_model *m, uint32_t n, const float *d_feat, cons
             for (uint32_t j = t - (t & 7); j <= t; ++j) h_losses[j] = l8[j & 7];
         }
     }
-    return cstat(cudaStreamSynchronize(s));
+    st = cstat(cudaStreamSynchronize(s));
+    if (!st) {
+        m->h_w.resize(NPARAM);
+        st = cstat(cudaMemcpy(m->h_w.data(), m->d_w, NPARAM * 4, cudaMemcpyDeviceToHost));
+    }
+    return st;
+}
+
+int gwfa_model_predict_host(const gwfa_model *m, const char *q, uint32_t n, uint32_t v_s, uint32_t v_e,
+                            float *h_pred) {
+    if (!m || !h_pred || (n && !q) || m->h_w.size() != (size_t)NPARAM) return GWFA_ERR_INVALID;
+    const uint32_t nv = m->g->nv;
+    if (v_s >= nv || v_e >= nv) return GWFA_ERR_INVALID;
+    // the same six features as features_kernel, from the ASCII query
+    std::vector<uint8_t> c(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        const char ch = q[i];
+        c[i] = (ch == 'C' || ch == 'c') ? 1 : (ch == 'G' || ch == 'g') ? 2 : (ch == 'T' || ch == 't') ? 3 : 0;
+    }
+    int miss = 0;
+    if (n >= (uint32_t)K) {
+        for (int t = 0; t < SAMPLES; ++t) {
+            const uint64_t p = (uint64_t)t * (n - K) / (SAMPLES - 1);
+            uint32_t key = 0;
+            for (int b = 0; b < K; ++b) key |= (uint32_t)c[p + b] << (2 * b);
+            miss += std::binary_search(m->h_kmers.begin(), m->h_kmers.end(), key) ? 0 : 1;
+        }
+    }
+    const uint32_t lo = std::min(v_s, v_e), hi = std::max(v_s, v_e);
+    const float f[F] = {std::log1p((float)n), n >= (uint32_t)K ? (float)miss / SAMPLES : 0.f,
+                        std::log1p((float)(hi - lo + 1)),
+                        std::log1p((float)(m->g->h_arc_off[hi + 1] - m->g->h_arc_off[lo])),
+                        (float)(m->h_bub[hi + 1] - m->h_bub[lo]) * 1000.f / (float)std::max(n, 1u),
+                        std::log1p((float)(m->h_back[hi + 1] - m->h_back[lo]))};
+    const float *w = m->h_w.data();
+    float x[F], h1[H], h2[H];
+    for (int i = 0; i < F; ++i) x[i] = (f[i] - m->norm.fmean[i]) / m->norm.fstd[i];
+    for (int o = 0; o < H; ++o) {
+        float a = w[OB1 + o];
+        for (int i = 0; i < F; ++i) a += w[OW1 + o * F + i] * x[i];
+        h1[o] = std::max(a, 0.f);
+    }
+    for (int o = 0; o < H; ++o) {
+        float a = w[OB2 + o];
+        for (int i = 0; i < H; ++i) a += w[OW2 + o * H + i] * h1[i];
+        h2[o] = std::max(a, 0.f);
+    }
+    for (int o = 0; o < O; ++o) {
+        float a = w[OB3 + o];
+        for (int i = 0; i < H; ++i) a += w[OW3 + o * H + i] * h2[i];
+        h_pred[o] = a * m->norm.tstd[o] + m->norm.tmean[o];
+    }
+    return GWFA_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,83 @@
+"""Open-loop load generation for the server: Poisson arrivals, p50/p99 latency.
+
+run_server(): requests are submitted at their arrival times and completions are
+polled in the same host loop (the server itself is the library's persistent
+kernel); latency = completion time seen by the host - arrival time.
+
+run_plain(): the baseline -- one synchronous single-query call (gwfa_align, one
+kernel launch each) at a time, in arrival order; a request waits for every
+earlier one.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+
+def _summary(lat: np.ndarray, bases: int, wall: float, n: int) -> dict:
+    return {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "throughput_qps": n / wall, "gbp_per_s": bases / wall / 1e9, "wall_s": wall}
+
+
+def run_server(server, queries, arrivals: np.ndarray, idx=None) -> tuple[dict, list]:
+    """Submit queries[idx[i]] at arrivals[i] (seconds from start); returns (summary, results)."""
+    idx = np.arange(len(arrivals)) if idx is None else np.asarray(idx)
+    n = len(arrivals)
+    qb = [queries.query(int(i)) for i in idx]
+    vs = [int(queries.v_s[i]) for i in idx]
+    ve = [int(queries.v_e[i]) for i in idx]
+    tickets = [None] * n
+    done_at = np.zeros(n)
+    results = [None] * n
+    pending = []
+    nxt = 0
+    t0 = time.perf_counter()
+    completed = 0
+    while completed < n:
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= now:
+            t = server.submit(qb[nxt], vs[nxt], ve[nxt])
+            if t is None:            # ring full: retry on the next pass
+                break
+            tickets[nxt] = t
+            pending.append(nxt)
+            nxt += 1
+        still = []
+        for i in pending:
+            r = server.poll(tickets[i])
+            if r is None:
+                still.append(i)
+            else:
+                results[i] = r
+                done_at[i] = time.perf_counter() - t0
+                completed += 1
+        pending = still
+        if not pending and nxt < n:
+            wait = arrivals[nxt] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 1e-3))
+    wall = time.perf_counter() - t0
+    lat = done_at - arrivals[:n]
+    bases = int(sum(len(q) for q in qb))
+    return _summary(lat, bases, wall, n), results
+
+
+def run_plain(graph, queries, arrivals: np.ndarray, idx=None, max_lag: int = 0) -> tuple[dict, list]:
+    """The same arrivals served by one synchronous gwfa_align call at a time."""
+    idx = np.arange(len(arrivals)) if idx is None else np.asarray(idx)
+    n = len(arrivals)
+    done_at = np.zeros(n)
+    results = []
+    t0 = time.perf_counter()
+    for k, i in enumerate(idx):
+        now = time.perf_counter() - t0
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        results.append(graph.align(queries.query(int(i)), int(queries.v_s[i]), int(queries.v_e[i]),
+                                   max_lag=max_lag))
+        done_at[k] = time.perf_counter() - t0
+    wall = time.perf_counter() - t0
+    bases = int(sum(int(queries.lengths()[i]) for i in idx))
+    return _summary(done_at - arrivals[:n], bases, wall, n), results
