@@ -207,6 +207,32 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n_queries, const uint32_t *
                             const uint32_t *d_order, uint32_t n_wide, const int32_t *d_status,
                             const gwfa_opts *opts, gwfa_result *d_out, void *stream);
 
+/*
+ * Allocation-free batch alignment (no counterpart in the paper: it exists for
+ * callers that cannot let a library allocate device memory -- code running
+ * inside a custom device-memory allocator, where calling back into allocation
+ * can deadlock or recurse; processes whose device memory another framework has
+ * reserved up front; loops that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation).  Same kernel and same results as gwfa_align_batch_device,
+ * but its scratch is one fixed 32 MiB device array inside the library (present
+ * on every GPU that loads it, until the process exits), carved into
+ * floor((32 MiB - 256 B) / slab) CTA slabs of 2^log2_tiles hash tiles each
+ * (log2_tiles 0 = 15: five CTAs in exact mode, three with pruning).  There is
+ * no overflow tier: a query needing more than 3/4 of its slab gets status
+ * GWFA_ERR_CAPACITY.  A log2_tiles whose slab does not fit the array is rejected
+ * with GWFA_ERR_CAPACITY before any GPU work.  Inputs and outputs are the
+ * caller's device buffers, laid out as for gwfa_align_batch_device (d_words
+ * from gwfa_pack_queries_device); the call only enqueues work on `stream`
+ * (NULL = the legacy default stream) and calls no allocation routine.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the array and resets it first, so calls whose GPU work overlaps race on it:
+ * the caller must serialise them (one stream, or its own ordering).
+ */
+int gwfa_align_noalloc(const gwfa_graph *g, uint32_t n_queries, const uint32_t *d_words,
+                       const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
+                       uint32_t log2_tiles, const gwfa_opts *opts, gwfa_result *d_out, void *stream);
+
 /* number of kernel launches the last batch call on this engine queued */
 uint32_t gwfa_engine_last_launches(const gwfa_engine *e);
 

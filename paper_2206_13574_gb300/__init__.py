@@ -121,6 +121,8 @@ class gwfa_server_stats(ctypes.Structure):
 
 
 SIGNATURES.update({
+    "gwfa_align_noalloc": ([_P, _u32, _P, _P, _P, _P, _u32, ctypes.POINTER(gwfa_opts), _P, _P],
+                           ctypes.c_int),
     "gwfa_model_predict_host": ([_P, _P, _u32, _u32, _u32, _P], ctypes.c_int),
     "gwfa_server_default_config": ([_P, ctypes.POINTER(gwfa_server_config)], ctypes.c_int),
     "gwfa_server_create": ([_P, ctypes.POINTER(gwfa_server_config), ctypes.POINTER(gwfa_opts), _P,
@@ -493,3 +495,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def align_noalloc(graph: Graph, batch: "DeviceBatch", log2_tiles: int = 0, max_lag: int = 0,
+                  max_score: int = -1, stream=None) -> int:
+    """gwfa_align_noalloc on a DeviceBatch, results into batch.out; returns the status.
+
+    For callers that cannot let the library allocate device memory: the scratch is a
+    fixed 32 MiB array inside the library, shared by all calls (serialise them)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream(batch.q.device)
+    o = _opts(max_lag, max_score)
+    return int(load().gwfa_align_noalloc(graph.handle, batch.n, batch.words.data_ptr(), batch.q_off.data_ptr(),
+                                         batch.v_s.data_ptr(), batch.v_e.data_ptr(), log2_tiles,
+                                         ctypes.byref(o), batch.out.data_ptr(), st.cuda_stream or None))
