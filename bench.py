@@ -127,6 +127,112 @@ def cpu_reference(args, g, qs, sample_s: float):
                       f"{t_total:.1f} s wall on {cores} threads"}
 
 
+def learned_schedule(gw, graph, qs, ref, stream, flush, args) -> dict:
+    """Cost model trained on logs of a separate config-2 batch (seed 12), then the
+    benchmark batch run in the planned order with predicted overflows on large slabs."""
+    import torch
+    from paper_2206_13574_gb300 import costmodel, synth
+    c2 = synth.CONFIGS[2]
+    g_synth = synth.make_graph(c2["graph"], 2)          # the benchmark graph itself
+    train_q = synth.make_queries(g_synth, 3000, 12, c2["length"], c2["div"], c2["weights"], c2["loops"])
+    model = gw.CostModel(graph, seed=1)
+    t0 = time.perf_counter()
+    eng0 = gw.Engine(graph)
+    feat, tgt, _ = costmodel.collect(model, eng0, train_q)
+    eng0.close()
+    costmodel.fit(model, feat, tgt, steps=1500, batch=512, lr=3e-3)
+    t_train = time.perf_counter() - t0
+    cfg = gw.default_config(graph)
+    # large-slab CTAs for the queries predicted to overflow tier 0; only as many are
+    # launched as there are such queries, so tier 0 keeps the whole GPU otherwise
+    cfg.wide.ctas, cfg.wide.log2_tiles, cfg.wide.threads = 152, 19, 512
+    eng = gw.Engine(graph, config=cfg)
+    with torch.cuda.stream(stream):
+        b = gw.DeviceBatch(qs, stream=stream)
+        feat = model.features(b, stream=stream)
+        pred = model.predict(feat, stream=stream)
+    stream.synchronize()
+    order, n_wide = gw.plan_schedule(pred.cpu().numpy(), int(0.75 * (1 << cfg.tiers[0].log2_tiles)))
+    with torch.cuda.stream(stream):
+        b2 = gw.DeviceBatch(qs, order=order, stream=stream)
+    ts = []
+    for it in range(args.warmup + max(3, args.steps // 2)):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b2.run(eng, stream=stream, n_wide=n_wide)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    r = b2.results()
+    assert np.array_equal(r["edit_distance"], ref["edit_distance"])
+    retries = int(eng.last_retries()[0])
+    t = float(np.mean(ts))
+    ok = r["status"] == 0
+    pred_np = pred.cpu().numpy()
+    eng.close()
+    return {"value": int(qs.lengths()[ok].sum()) / t / 1e9, "unit": UNIT, "ms_per_step": t * 1e3,
+            "n_wide": n_wide, "tier0_overflows": retries, "train_s": t_train,
+            "spearman_cells": costmodel.spearman(pred_np[:, 3], np.log1p(ref["cells"].astype(np.float64))),
+            "train": "3000 other queries on the same graph (query seed 12), 1500 Adam steps on the GPU"}
+
+
+def serving_run(gw, graph, qs, ref, rates=(2000.0, 20000.0), duration=0.5) -> dict:
+    """p50/p99 latency and throughput of the continuous-batching server at two rates."""
+    from paper_2206_13574_gb300 import serving, synth
+    srv = gw.Server(graph)
+    out = {}
+    for lam in rates:
+        arr = synth.poisson_arrivals(lam, duration, seed=int(lam))
+        idx = np.arange(len(arr)) % len(qs)
+        summ, res = serving.run_server(srv, qs, arr, idx)
+        assert all(x["edit_distance"] == int(ref["edit_distance"][i]) for x, i in zip(res, idx))
+        out[f"lambda_{int(lam)}"] = summ
+    out["server"] = srv.stats()
+    srv.close()
+    return out
+
+
+def ncu_case(args):
+    """The benchmark kernel on a case small enough for a multi-pass ncu capture."""
+    import torch
+    import paper_2206_13574_gb300 as gw
+    from paper_2206_13574_gb300 import _build, synth
+    _build.build()
+    g, qs = synth.make_config(2, n_queries=args.queries or 2000)
+    graph = gw.Graph.from_synth(g)
+    c = gw.default_config(graph)
+    c.tiers[0].log2_tiles = 14
+    c.tiers[1].ctas, c.tiers[1].log2_tiles = 16, 18
+    c.tiers[2].ctas, c.tiers[2].log2_tiles = 1, 21
+    eng = gw.Engine(graph, config=c)
+    b = gw.DeviceBatch(qs, order=np.argsort(-qs.lengths(), kind="stable").astype(np.uint32))
+    for _ in range(2):
+        b.run(eng)
+    torch.cuda.synchronize()
+    r = b.results()
+    print(json.dumps({"ncu_case": True, "engine_bytes": eng.device_bytes, "ok": int((r["status"] == 0).sum()),
+                      "cells": int(r["cells"].sum()), "bases": int(qs.lengths().sum())}))
+
+
+def measured_traffic_per_cell():
+    """DRAM bytes per cell from the committed ncu summary, if it was taken on the
+    current kernel source (else None: the counters no longer describe this kernel)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "align_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2206_13574_gb300", "csrc", "gwfa_kernels.cu")
+    if not os.path.exists(p):
+        return None, None
+    d = json.load(open(p))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("kernel_source_sha256") != sha:
+        return None, d.get("source")
+    return float(d["dram_bytes_per_cell"]), d.get("source")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -137,11 +243,17 @@ def main():
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-wide", type=int, default=0, help="queries on the wide CTA class")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain / learned / serving legs")
+    ap.add_argument("--plain-sample", type=int, default=300)
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="small profiling case: --queries (default 2000) on ~3 GB of slabs, two batches")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     ws, rank, local = _dist()
     from paper_2206_13574_gb300 import synth
+    if args.ncu_case:
+        return ncu_case(args)
     g, qs = synth.make_config(2, n_queries=args.queries)
     total_bp = int(qs.lengths().sum())
 
@@ -268,6 +380,31 @@ def main():
     alg_bytes = B_CELL * cells + 0.5 * aligned_bp
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_step / 1e9
+    tpc, tsrc = measured_traffic_per_cell()
+
+    # S4: the plain path (one launch per query, synchronous) on a random sample
+    plain = None
+    if not args.no_extras:
+        rng = np.random.default_rng(99)
+        sidx = rng.choice(len(qs), size=min(args.plain_sample, len(qs)), replace=False)
+        t0 = time.perf_counter()
+        for i in sidx:
+            r = graph.align(qs.query(int(i)), int(qs.v_s[i]), int(qs.v_e[i]))
+            assert r["edit_distance"] == int(res["edit_distance"][i])
+        tp = time.perf_counter() - t0
+        pbp = int(qs.lengths()[sidx].sum())
+        plain = {"value": pbp / tp / 1e9, "unit": UNIT, "sample": f"{len(sidx)} random queries",
+                 "ms_per_query": tp / len(sidx) * 1e3}
+
+    # S2: the learned schedule (cost model trained on a separate seeded batch)
+    learned = None
+    if not args.no_extras:
+        learned = learned_schedule(gw, graph, qs, res, stream, flush, args)
+
+    # S3: serving on the resident graph, Poisson arrivals
+    serving_out = None
+    if not args.no_extras:
+        serving_out = serving_run(gw, graph, qs, res)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -294,13 +431,21 @@ def main():
                     "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (tpc * cells) if tpc is not None else None,
+                         "traffic_note": ("ncu dram read+write per cell on a 2,000-query case, scaled to "
+                                          f"this step's cells ({tsrc})") if tpc is not None else
+                                         "no ncu counters for the current kernel source",
                          "peak_kind": f"{peak_kind} HBM copy",
                          "kernel": "align_kernel<exact> (all tiers of one step)",
                          "bytes_per_cell": B_CELL},
             "cells_per_s": cells * ws / t_step,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "plain": plain,
+            "batched_vs_plain": (value / plain["value"]) if plain else None,
+            "learned_schedule": learned,
+            "serving": serving_out,
         }
         print(json.dumps(line))
     if ws > 1:

@@ -355,6 +355,10 @@ int gwfa_submit(gwfa_server *s, const char *h_q, uint32_t n, uint32_t v_s, uint3
                 uint64_t *ticket);
 /* GWFA_OK with *out filled (once per ticket), or GWFA_PENDING */
 int gwfa_poll(gwfa_server *s, uint64_t ticket, gwfa_result *out);
+/* gwfa_poll over tickets[i] whose done_flags[i] is 0: finished ones get out[i] and
+ * done_flags[i] = 1; *n_done = how many finished in this call */
+int gwfa_poll_many(gwfa_server *s, uint32_t n, const uint64_t *tickets, gwfa_result *out,
+                   uint8_t *done_flags, uint32_t *n_done);
 /* polls until done or timeout_ms (GWFA_ERR_TIMEOUT) */
 int gwfa_wait(gwfa_server *s, uint64_t ticket, uint32_t timeout_ms, gwfa_result *out);
 int gwfa_server_get_stats(gwfa_server *s, gwfa_server_stats *out);

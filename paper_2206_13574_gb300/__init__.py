@@ -130,6 +130,7 @@ SIGNATURES.update({
     "gwfa_submit": ([_P, _P, _u32, _u32, _u32, ctypes.POINTER(_u64)], ctypes.c_int),
     "gwfa_poll": ([_P, _u64, ctypes.POINTER(gwfa_result)], ctypes.c_int),
     "gwfa_wait": ([_P, _u64, _u32, ctypes.POINTER(gwfa_result)], ctypes.c_int),
+    "gwfa_poll_many": ([_P, _u32, _P, _P, _P, ctypes.POINTER(_u32)], ctypes.c_int),
     "gwfa_server_get_stats": ([_P, ctypes.POINTER(gwfa_server_stats)], ctypes.c_int),
     "gwfa_server_destroy": ([_P], ctypes.c_int),
 })
@@ -474,6 +475,13 @@ class Server:
             return None
         _check(st, "gwfa_poll")
         return r.as_dict()
+
+    def poll_many(self, tickets: np.ndarray, out: np.ndarray, done: np.ndarray) -> int:
+        """Poll every ticket not yet done; results into out (RESULT_DTYPE), flags into done."""
+        k = _u32()
+        _check(load().gwfa_poll_many(self.handle, len(tickets), tickets.ctypes.data, out.ctypes.data,
+                                     done.ctypes.data, ctypes.byref(k)), "gwfa_poll_many")
+        return int(k.value)
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
         r = gwfa_result()

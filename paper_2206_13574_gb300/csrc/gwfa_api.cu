@@ -474,6 +474,14 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
     e->last_launches = 0;
     if (!e->wide_slabs) n_wide = 0;
     n_wide = std::min(n_wide, n);
+    // wide and tier-0 CTAs must be resident together (tier 0 would otherwise fill
+    // every SM slot first and the heaviest queries would start only after it):
+    // tier 0 gives up the room of the wide CTAs it runs beside
+    const uint32_t t0_threads = e->cfg.tiers[0].threads ? e->cfg.tiers[0].threads : e->cfg.threads;
+    const uint32_t w_threads = e->cfg.wide.threads ? e->cfg.wide.threads : e->cfg.threads;
+    const uint32_t wctas = n_wide ? std::min(e->cfg.wide.ctas, n_wide) : 0;
+    const uint32_t t0_yield = (uint32_t)(((uint64_t)wctas * w_threads + t0_threads - 1) / t0_threads);
+    const uint32_t t0_ctas = e->cfg.tiers[0].ctas > t0_yield ? e->cfg.tiers[0].ctas - t0_yield : 1;
     if (n_wide > 0) {
         // the heaviest queries on wide CTAs, concurrently with tier 0 on the rest;
         // their capacity failures join tier 0's retry list
@@ -500,8 +508,7 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
         a.stats = e->stats;
         st = cuda_status(cudaEventRecord(e->ev_fork, s));
         if (!st) st = cuda_status(cudaStreamWaitEvent(e->side, e->ev_fork, 0));
-        const uint32_t th = e->cfg.wide.threads ? e->cfg.wide.threads : e->cfg.threads;
-        if (!st) st = cuda_status(gwfa::launch_align(a, prune, e->cfg.wide.ctas, th, e->side));
+        if (!st) st = cuda_status(gwfa::launch_align(a, prune, wctas, w_threads, e->side));
         if (!st) st = cuda_status(cudaEventRecord(e->ev_join, e->side));
         if (st) return st;
         e->last_launches++;
@@ -533,7 +540,7 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
         a.max_score = o.max_score;
         a.stats = e->stats;
         const uint32_t th = e->cfg.tiers[t].threads ? e->cfg.tiers[t].threads : e->cfg.threads;
-        st = cuda_status(gwfa::launch_align(a, prune, e->cfg.tiers[t].ctas, th, s));
+        st = cuda_status(gwfa::launch_align(a, prune, t == 0 ? t0_ctas : e->cfg.tiers[t].ctas, th, s));
         if (st) return st;
         e->last_launches++;
     }

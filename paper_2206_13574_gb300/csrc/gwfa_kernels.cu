@@ -775,7 +775,7 @@ __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned l
 // wait is bounded: a CTA that finds no request for wait_limit polls (or sees the
 // stop flag) leaves the loop, and the host relaunches the kernel when work comes.
 template <bool P>
-__global__ void __launch_bounds__(512, 2) server_kernel(ServerArgs S) {
+__global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
     extern __shared__ uint32_t qsm[];   // the request's packed words, staged
     __shared__ Sh sh;
     __shared__ unsigned long long s_ticket;

@@ -144,7 +144,7 @@ int gwfa_server_default_config(const gwfa_graph *g, gwfa_server_config *c) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
         return GWFA_ERR_CUDA;
     c->threads = 512;
-    c->ctas_small = (uint32_t)sms * 2 - (uint32_t)std::max(sms / 8, 1);
+    c->ctas_small = (uint32_t)sms * 4 - (uint32_t)std::max(sms / 8, 1);
     c->ctas_big = (uint32_t)std::max(sms / 8, 1);
     c->log2_small = 16;
     c->log2_big = 21;
@@ -323,6 +323,24 @@ int gwfa_poll(gwfa_server *sv, uint64_t ticket, gwfa_result *out) {
     if (it != sv->redirect.end()) sv->redirect.erase(it);
     sv->n_completed++;
     *out = r;
+    return GWFA_OK;
+}
+
+int gwfa_poll_many(gwfa_server *sv, uint32_t n, const uint64_t *tickets, gwfa_result *out,
+                   uint8_t *done_flags, uint32_t *n_done) {
+    if (!sv || (n && (!tickets || !out || !done_flags)) || !n_done) return GWFA_ERR_INVALID;
+    uint32_t k = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (done_flags[i]) continue;
+        const int st = gwfa_poll(sv, tickets[i], out + i);
+        if (st == GWFA_OK) {
+            done_flags[i] = 1;
+            ++k;
+        } else if (st != GWFA_PENDING) {
+            return st;
+        }
+    }
+    *n_done = k;
     return GWFA_OK;
 }
 

@@ -23,18 +23,19 @@ def _summary(lat: np.ndarray, bases: int, wall: float, n: int) -> dict:
 
 def run_server(server, queries, arrivals: np.ndarray, idx=None) -> tuple[dict, list]:
     """Submit queries[idx[i]] at arrivals[i] (seconds from start); returns (summary, results)."""
+    from . import RESULT_DTYPE
     idx = np.arange(len(arrivals)) if idx is None else np.asarray(idx)
     n = len(arrivals)
     qb = [queries.query(int(i)) for i in idx]
     vs = [int(queries.v_s[i]) for i in idx]
     ve = [int(queries.v_e[i]) for i in idx]
-    tickets = [None] * n
+    tickets = np.zeros(n, dtype=np.uint64)
+    out = np.zeros(n, dtype=RESULT_DTYPE)
+    done = np.zeros(n, dtype=np.uint8)
     done_at = np.zeros(n)
-    results = [None] * n
-    pending = []
     nxt = 0
-    t0 = time.perf_counter()
     completed = 0
+    t0 = time.perf_counter()
     while completed < n:
         now = time.perf_counter() - t0
         while nxt < n and arrivals[nxt] <= now:
@@ -42,25 +43,22 @@ def run_server(server, queries, arrivals: np.ndarray, idx=None) -> tuple[dict, l
             if t is None:            # ring full: retry on the next pass
                 break
             tickets[nxt] = t
-            pending.append(nxt)
             nxt += 1
-        still = []
-        for i in pending:
-            r = server.poll(tickets[i])
-            if r is None:
-                still.append(i)
-            else:
-                results[i] = r
-                done_at[i] = time.perf_counter() - t0
-                completed += 1
-        pending = still
-        if not pending and nxt < n:
+        if nxt:
+            before = done[:nxt].copy()
+            k = server.poll_many(tickets[:nxt], out[:nxt], done[:nxt])
+            if k:
+                t_done = time.perf_counter() - t0
+                done_at[:nxt][(done[:nxt] == 1) & (before == 0)] = t_done
+                completed += k
+        if completed < n and nxt < n and nxt == completed:
             wait = arrivals[nxt] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(min(wait, 1e-3))
     wall = time.perf_counter() - t0
     lat = done_at - arrivals[:n]
     bases = int(sum(len(q) for q in qb))
+    results = [{f: int(out[i][f]) for f in RESULT_DTYPE.names} for i in range(n)]
     return _summary(lat, bases, wall, n), results
 
 

@@ -208,3 +208,48 @@ def test_edge_cases():
     # max_score stops the loop
     r = graph.align(b"TTTTTTTTTTTT", 0, 0, max_score=2)
     assert r["status"] == gw.GWFA_ERR_SCORE_LIMIT
+
+
+def test_device_batch_replays_as_cuda_graph():
+    """The device-resident batch call (counter reset + tier launches, no host sync) is
+    captured once into a CUDA graph and replayed; results match the direct call."""
+    import torch
+    g, qs = synth.make_config(2, n_queries=300)
+    graph = gw.Graph.from_synth(g)
+    eng = gw.Engine(graph)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        b = gw.DeviceBatch(qs, stream=st)
+        b.run(eng, stream=st)          # sizes internal buffers outside the capture
+    st.synchronize()
+    direct = b.results()
+    graph_obj = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_obj, stream=st):
+        b.run(eng, stream=torch.cuda.current_stream())
+    for _ in range(2):
+        b.out.zero_()
+        graph_obj.replay()
+        torch.cuda.synchronize()
+        rep = b.results()
+        for f in gw.RESULT_DTYPE.names:
+            if f != "device_us":
+                assert np.array_equal(rep[f], direct[f]), f
+
+
+def test_autotuner_persists_and_keeps_results(tmp_path):
+    from paper_2206_13574_gb300 import autotune
+    g, qs = synth.make_config(2, n_queries=400)
+    graph = gw.Graph.from_synth(g)
+    sample = qs.subset(np.arange(0, 400, 2))
+    path = str(tmp_path / "tune.json")
+    t = autotune.autotune(graph, sample, threads=(256, 512), per_sm_frac=(1.0,), log2_tiles=(15, 16),
+                          reps=1, cache_path=path)
+    assert len(t["trials"]) == 4 and t["best"]["ms"] == min(x["ms"] for x in t["trials"])
+    again = autotune.autotune(graph, sample, cache_path=path)      # served from the JSON cache
+    assert again["best"] == t["best"]
+    eng = gw.Engine(graph, config=autotune.apply(graph, t))
+    rest = qs.subset(np.arange(1, 400, 2))
+    res = eng.align_batch(rest.seq, rest.off, rest.v_s, rest.v_e)
+    want = oracle.gwfa_many(g, rest, range(0, len(rest), 9))
+    for i, w in zip(range(0, len(rest), 9), want):
+        assert_same(res[i], w, f"q{i}")
