@@ -55,7 +55,9 @@ const char *gwfa_strerror(int status);
 /* ---- options and results ------------------------------------------------ */
 typedef struct {
     int32_t max_lag;     /* a_diff of Alg. 4 (Sec. 2.5); 0 = exact (no pruning) */
-    int32_t traceback;   /* reserved, must be 0 */
+    int32_t traceback;   /* 1: record the alignment walk (Alg. 5-6); needs max_lag == 0 and
+                            64-bit slabs (engine prune_slabs); see gwfa_align_path /
+                            gwfa_engine_set_paths */
     int32_t max_score;   /* stop with GWFA_ERR_SCORE_LIMIT once d would exceed it; -1 = no limit */
     int32_t wait_limit;  /* serving: iteration limit of device-side waits; 0 = default */
 } gwfa_opts;
@@ -124,6 +126,17 @@ int gwfa_graph_get_info(const gwfa_graph *g, gwfa_graph_info *out);
  */
 int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t v_s, uint32_t v_e,
                const gwfa_opts *opts, gwfa_result *out);
+
+/*
+ * gwfa_align with the optimal walk (Alg. 5-6): the vertices of one s->e walk
+ * whose spelled sequence is at edit distance out->edit_distance from the query
+ * (several optimal walks may exist; this returns one).  h_path[path_cap] gets
+ * the first min(path_cap, *path_len) vertex ids; *path_len is the full length.
+ * opts->max_lag must be 0 (traceback with pruning is not supported).
+ */
+int gwfa_align_path(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t v_s, uint32_t v_e,
+                    const gwfa_opts *opts, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
+                    uint32_t *path_len);
 
 /* ---- batched path: persistent kernel with a device work queue ----------- */
 typedef struct gwfa_engine gwfa_engine;
@@ -232,6 +245,11 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n_queries, const uint32_t *
 int gwfa_align_noalloc(const gwfa_graph *g, uint32_t n_queries, const uint32_t *d_words,
                        const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
                        uint32_t log2_tiles, const gwfa_opts *opts, gwfa_result *d_out, void *stream);
+
+/* Walk output of later batch calls with opts.traceback = 1: query i writes its
+ * walk to d_paths[i * path_cap ...] (at most path_cap ids) and its full length to
+ * d_path_len[i]; both device buffers are the caller's (NULL / 0 = off). */
+int gwfa_engine_set_paths(gwfa_engine *e, uint32_t *d_paths, uint32_t path_cap, uint32_t *d_path_len);
 
 /* number of kernel launches the last batch call on this engine queued */
 uint32_t gwfa_engine_last_launches(const gwfa_engine *e);

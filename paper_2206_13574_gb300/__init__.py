@@ -123,6 +123,9 @@ class gwfa_server_stats(ctypes.Structure):
 SIGNATURES.update({
     "gwfa_align_noalloc": ([_P, _u32, _P, _P, _P, _P, _u32, ctypes.POINTER(gwfa_opts), _P, _P],
                            ctypes.c_int),
+    "gwfa_align_path": ([_P, _P, _u32, _u32, _u32, ctypes.POINTER(gwfa_opts), ctypes.POINTER(gwfa_result),
+                         _P, _u32, ctypes.POINTER(_u32)], ctypes.c_int),
+    "gwfa_engine_set_paths": ([_P, _P, _u32, _P], ctypes.c_int),
     "gwfa_model_predict_host": ([_P, _P, _u32, _u32, _u32, _P], ctypes.c_int),
     "gwfa_server_default_config": ([_P, ctypes.POINTER(gwfa_server_config)], ctypes.c_int),
     "gwfa_server_create": ([_P, ctypes.POINTER(gwfa_server_config), ctypes.POINTER(gwfa_opts), _P,
@@ -180,8 +183,8 @@ def _c(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
-def _opts(max_lag: int, max_score: int) -> gwfa_opts:
-    return gwfa_opts(int(max_lag), 0, int(max_score), 0)
+def _opts(max_lag: int, max_score: int, traceback: int = 0) -> gwfa_opts:
+    return gwfa_opts(int(max_lag), int(traceback), int(max_score), 0)
 
 
 class Graph:
@@ -217,6 +220,17 @@ class Graph:
         _check(load().gwfa_align(self.handle, qb, len(qb), v_s, v_e, ctypes.byref(o), ctypes.byref(r)),
                "gwfa_align")
         return r.as_dict()
+
+    def align_path(self, q: bytes, v_s: int, v_e: int, max_score: int = -1, path_cap: int = 1 << 16):
+        """(result, walk) with the optimal walk's vertex ids (gwfa_align_path)."""
+        r = gwfa_result()
+        o = _opts(0, max_score)
+        qb = bytes(q)
+        path = np.zeros(path_cap, dtype=np.uint32)
+        plen = _u32()
+        _check(load().gwfa_align_path(self.handle, qb, len(qb), v_s, v_e, ctypes.byref(o), ctypes.byref(r),
+                                      path.ctypes.data, path_cap, ctypes.byref(plen)), "gwfa_align_path")
+        return r.as_dict(), path[:min(plen.value, path_cap)].copy()
 
     def close(self):
         if getattr(self, "handle", None):
@@ -263,6 +277,11 @@ class Engine:
         _check(load().gwfa_engine_last_retries(self.handle, out.ctypes.data), "gwfa_engine_last_retries")
         return out
 
+    def set_paths(self, d_paths: int | None, path_cap: int = 0, d_path_len: int | None = None):
+        """Walk output for batches with traceback (device buffers, or None to stop)."""
+        _check(load().gwfa_engine_set_paths(self.handle, d_paths or None, path_cap, d_path_len or None),
+               "gwfa_engine_set_paths")
+
     def set_stats(self, d_stats: int | None):
         """Per-query statistics into device memory (8 uint64 per query id), or None to stop."""
         _check(load().gwfa_engine_set_stats(self.handle, d_stats or None), "gwfa_engine_set_stats")
@@ -286,9 +305,10 @@ class Engine:
 
     def align_batch_device(self, n: int, d_words: int, d_q_off: int, d_v_s: int, d_v_e: int,
                            d_order: int | None, d_status: int | None, d_out: int,
-                           max_lag: int = 0, max_score: int = -1, stream: int = 0, n_wide: int = 0):
+                           max_lag: int = 0, max_score: int = -1, stream: int = 0, n_wide: int = 0,
+                           traceback: bool = False):
         """Device pointers in and out, asynchronous on `stream` (gwfa_align_batch_device)."""
-        o = _opts(max_lag, max_score)
+        o = _opts(max_lag, max_score, int(traceback))
         _check(load().gwfa_align_batch_device(self.handle, n, d_words, d_q_off, d_v_s, d_v_e,
                                               d_order or None, n_wide, d_status or None, ctypes.byref(o),
                                               d_out, stream or None),
@@ -338,14 +358,15 @@ class DeviceBatch:
         pack_queries_device(self.n, self.q.data_ptr(), self.q_off.data_ptr(), self.words.data_ptr(),
                             self.status.data_ptr(), st.cuda_stream)
 
-    def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None, n_wide: int = 0):
+    def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None, n_wide: int = 0,
+            traceback: bool = False):
         import torch
         st = stream if stream is not None else torch.cuda.current_stream(self.q.device)
         engine.align_batch_device(self.n, self.words.data_ptr(), self.q_off.data_ptr(),
                                   self.v_s.data_ptr(), self.v_e.data_ptr(),
                                   None if self.order is None else self.order.data_ptr(),
                                   self.status.data_ptr(), self.out.data_ptr(), max_lag, max_score,
-                                  st.cuda_stream, n_wide)
+                                  st.cuda_stream, n_wide, traceback)
 
     def results(self) -> np.ndarray:
         return self.out.cpu().numpy().view(RESULT_DTYPE)

@@ -213,13 +213,35 @@ int gwfa_graph_get_info(const gwfa_graph *g, gwfa_graph_info *o) {
 
 // ---------------------------------------------------------------- plain path
 
+static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
+                       const gwfa_opts &o, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
+                       uint32_t *path_len);
+
 int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
                const gwfa_opts *opts, gwfa_result *out) {
-    if (!g || !out || (n > 0 && !h_q)) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
+    if (o.traceback != 0) return GWFA_ERR_INVALID;   // the walk needs gwfa_align_path
+    return align_plain(g, h_q, n, vs, ve, o, out, nullptr, 0, nullptr);
+}
+
+int gwfa_align_path(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
+                    const gwfa_opts *opts, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
+                    uint32_t *path_len) {
+    gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
+    if (o.max_lag != 0 || !path_len || (path_cap && !h_path)) return GWFA_ERR_INVALID;
+    o.traceback = 1;
+    return align_plain(g, h_q, n, vs, ve, o, out, h_path, path_cap, path_len);
+}
+
+static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
+                       const gwfa_opts &o, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
+                       uint32_t *path_len) {
+    if (!g || !out || (n > 0 && !h_q)) return GWFA_ERR_INVALID;
     memset(out, 0, sizeof(*out));
     out->edit_distance = -1;
-    if (vs >= g->nv || ve >= g->nv || o.max_lag < 0 || o.traceback != 0 || n >= 0x7FFFFFFFu) {
+    if (path_len) *path_len = 0;
+    if (vs >= g->nv || ve >= g->nv || o.max_lag < 0 || n >= 0x7FFFFFFFu ||
+        (o.traceback && o.max_lag != 0)) {
         out->status = GWFA_ERR_INVALID;
         return GWFA_ERR_INVALID;
     }
@@ -230,10 +252,10 @@ int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, ui
     std::lock_guard<std::mutex> lk(g->mu);
     int st = cuda_status(cudaSetDevice(g->device));
     if (st) return st;
-    const bool prune = o.max_lag > 0;
-    // staging: query bytes | q_off[2] | v_s | v_e | words | status | head | result
-    const uint64_t need = gwfa::align256(n + 16) + 256 * 5 + gwfa::align256(words_for(1, n) * 4) +
-                          gwfa::align256(sizeof(gwfa_result)) + 1024;
+    const bool prune = o.max_lag > 0 || o.traceback;   // 64-bit values (base or trace payload)
+    // staging: query bytes | q_off[2] | v_s | v_e | words | status | head | result | path
+    const uint64_t need = gwfa::align256(n + 16) + 256 * 6 + gwfa::align256(words_for(1, n) * 4) +
+                          gwfa::align256(sizeof(gwfa_result)) + gwfa::align256((uint64_t)path_cap * 4) + 1024;
     st = ensure(&g->plain_stage, &g->plain_stage_bytes, need);
     if (st) return st;
     Carve c{g->plain_stage};
@@ -245,6 +267,8 @@ int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, ui
     uint32_t *d_head = c.take<uint32_t>(4);
     gwfa_result *d_res = c.take<gwfa_result>(sizeof(gwfa_result));
     uint32_t *d_words = c.take<uint32_t>(words_for(1, n) * 4);
+    uint32_t *d_plen = c.take<uint32_t>(4);
+    uint32_t *d_path = c.take<uint32_t>((uint64_t)path_cap * 4);
     uint64_t h_off[2] = {0, n};
     cudaStream_t s = g->stream;
     uint32_t log2 = g->plain_log2 && g->plain_prune == prune ? g->plain_log2 : (prune ? 15u : 16u);
@@ -286,10 +310,19 @@ int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, ui
         a.log2cap = log2;
         a.max_lag = o.max_lag;
         a.max_score = o.max_score;
+        a.traceback = o.traceback ? 1 : 0;
+        a.paths = o.traceback ? d_path : nullptr;
+        a.path_len = o.traceback ? d_plen : nullptr;
+        a.path_cap = path_cap;
+        if (o.traceback) cudaMemsetAsync(d_plen, 0, 4, s);
         st = cuda_status(gwfa::launch_align(a, prune, 1, 512, s));
         if (st) return st;
         st = cuda_status(cudaMemcpyAsync(out, d_res, sizeof(gwfa_result), cudaMemcpyDeviceToHost, s));
+        if (!st && o.traceback) st = cuda_status(cudaMemcpyAsync(path_len, d_plen, 4, cudaMemcpyDeviceToHost, s));
         if (!st) st = cuda_status(cudaStreamSynchronize(s));
+        if (!st && o.traceback && path_cap && *path_len)
+            st = cuda_status(cudaMemcpy(h_path, d_path, (uint64_t)std::min(path_cap, *path_len) * 4,
+                                        cudaMemcpyDeviceToHost));
         if (st) return st;
         if (out->status == GWFA_ERR_CAPACITY && log2 + 3 <= gwfa::kMaxLog2Tiles) {
             log2 += 3;   // grow the workspace and run again
@@ -445,6 +478,15 @@ int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, ui
     return GWFA_OK;
 }
 
+int gwfa_engine_set_paths(gwfa_engine *e, uint32_t *d_paths, uint32_t path_cap, uint32_t *d_path_len) {
+    if (!e || (path_cap && !d_paths)) return GWFA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->paths = d_paths;
+    e->path_cap = path_cap;
+    e->path_len = d_path_len;
+    return GWFA_OK;
+}
+
 int gwfa_engine_set_stats(gwfa_engine *e, uint64_t *d_stats) {
     if (!e) return GWFA_ERR_INVALID;
     std::lock_guard<std::mutex> lk(e->mu);
@@ -470,7 +512,7 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
     uint32_t *wide_head = e->counters + 2 * GWFA_MAX_TIERS;
     st = cuda_status(cudaMemsetAsync(e->counters, 0, 256, s));
     if (st) return st;
-    const bool prune = o.max_lag > 0;
+    const bool prune = o.max_lag > 0 || o.traceback;   // 64-bit values
     e->last_launches = 0;
     if (!e->wide_slabs) n_wide = 0;
     n_wide = std::min(n_wide, n);
@@ -506,6 +548,10 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
         a.max_lag = o.max_lag;
         a.max_score = o.max_score;
         a.stats = e->stats;
+        a.traceback = o.traceback ? 1 : 0;
+        a.paths = e->paths;
+        a.path_len = e->path_len;
+        a.path_cap = e->path_cap;
         st = cuda_status(cudaEventRecord(e->ev_fork, s));
         if (!st) st = cuda_status(cudaStreamWaitEvent(e->side, e->ev_fork, 0));
         if (!st) st = cuda_status(gwfa::launch_align(a, prune, wctas, w_threads, e->side));
@@ -539,6 +585,10 @@ static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const 
         a.max_lag = o.max_lag;
         a.max_score = o.max_score;
         a.stats = e->stats;
+        a.traceback = o.traceback ? 1 : 0;
+        a.paths = e->paths;
+        a.path_len = e->path_len;
+        a.path_cap = e->path_cap;
         const uint32_t th = e->cfg.tiers[t].threads ? e->cfg.tiers[t].threads : e->cfg.threads;
         st = cuda_status(gwfa::launch_align(a, prune, t == 0 ? t0_ctas : e->cfg.tiers[t].ctas, th, s));
         if (st) return st;
@@ -557,8 +607,8 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
                             const gwfa_opts *opts, gwfa_result *d_out, void *stream) {
     if (!e || !d_words || !d_q_off || !d_vs || !d_ve || !d_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || o.traceback != 0) return GWFA_ERR_INVALID;
-    if (o.max_lag > 0 && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0)) return GWFA_ERR_INVALID;
+    if ((o.max_lag > 0 || o.traceback) && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
     if (n == 0) return GWFA_OK;
     std::lock_guard<std::mutex> lk(e->mu);
     int st = cuda_status(cudaSetDevice(e->g->device));
@@ -574,8 +624,8 @@ int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t
                      uint32_t n_wide, const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
     if (!e || !h_q_off || !h_vs || !h_ve || !h_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || o.traceback != 0) return GWFA_ERR_INVALID;
-    if (o.max_lag > 0 && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0)) return GWFA_ERR_INVALID;
+    if ((o.max_lag > 0 || o.traceback) && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
     if (n == 0) return GWFA_OK;
     if (h_q_off[0] != 0) return GWFA_ERR_INVALID;
     const uint64_t nb = h_q_off[n];

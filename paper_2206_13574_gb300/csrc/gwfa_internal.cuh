@@ -62,7 +62,7 @@ struct alignas(sizeof(T) == 4 ? 64 : 128) EEntT {
 
 // Per-CTA slab layout (all arrays 256-byte aligned), cap = 2^log2 tiles.
 struct SlabLayout {
-    uint64_t slots, touched, qlist, slist0, slist1, elist, req, total, slot_bytes;
+    uint64_t slots, touched, qlist, slist0, slist1, elist, req, trace, total, slot_bytes;
 };
 
 __host__ __device__ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -81,6 +81,7 @@ __host__ __device__ inline SlabLayout slab_layout(uint32_t log2cap, bool prune) 
     L.slist1 = o;  o = align256(o + cap * sizeof(LEnt));
     L.elist = o;   o = align256(o + cap * eb);
     L.req = o;     o = align256(o + (prune ? cap * 16 : 0));
+    L.trace = o;   o = align256(o + (prune ? cap * 2 * 8 : 0));   // Alg. 5's T: (v, t) pairs
     L.total = o;
     return L;
 }
@@ -107,6 +108,10 @@ struct TierArgs {
     int32_t max_score;
     unsigned long long *stats;  // optional, kStatWords per query id (see gwfa_engine_set_stats)
     int q_smem;                 // query words are in shared memory (server kernel)
+    int traceback;              // 64-bit values carry a trace index (Alg. 5-6) instead of a base
+    uint32_t *paths;            // traceback: path_cap vertex ids per query id
+    uint32_t *path_len;         // traceback: walk length per query id (may exceed path_cap)
+    uint32_t path_cap;
 };
 constexpr int kStatWords = 8;
 
@@ -194,5 +199,7 @@ struct gwfa_engine {
     uint64_t device_bytes = 0;
     uint32_t last_launches = 0;
     unsigned long long *stats = nullptr;
+    uint32_t *paths = nullptr, *path_len = nullptr;
+    uint32_t path_cap = 0;
     std::mutex mu;
 };

@@ -46,6 +46,7 @@ namespace {
 constexpr long long kTagPend = 0, kTagFresh = 1, kTagSettled = 2;
 constexpr uint32_t kBaseMask = 0x3FFFFFFFu;
 constexpr int kStack = 6;   // depth-first spill stack per thread (exact mode)
+constexpr uint32_t kNoTrace = 0x3FFFFFFFu;   // trace index of the start diagonal (no predecessor)
 
 template <bool P> struct VT;
 template <> struct VT<false> { using T = int; };
@@ -66,6 +67,7 @@ template <bool P> struct Slab {
     LEnt *qlist, *slist[2];
     EEntT<T> *elist;
     int4 *req;
+    uint2 *trace;
     uint32_t cap, mask;
 };
 
@@ -80,6 +82,7 @@ __device__ __forceinline__ Slab<P> carve(uint8_t *base, uint32_t log2cap) {
     s.slist[1] = (LEnt *)(base + L.slist1);
     s.elist = (EEntT<typename VT<P>::T> *)(base + L.elist);
     s.req = (int4 *)(base + L.req);
+    s.trace = (uint2 *)(base + L.trace);
     s.cap = 1u << log2cap;
     s.mask = s.cap - 1;
     return s;
@@ -100,6 +103,8 @@ struct Sh {
     unsigned long long cells, visited, pruned, spills;
     uint32_t peak;
     uint32_t claim[3];  // work counters of the phases, rotating (see align_one)
+    uint32_t tlen;      // traceback: entries of T
+    uint32_t end_payload;
 };
 
 __device__ __forceinline__ void set_err(Sh &sh, int code) { atomicCAS(&sh.err, 0, code); }
@@ -370,13 +375,27 @@ __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &
     }
 }
 
+// GwfPushTrace (Alg. 5): record "vertex v, reached with trace t" and return its
+// index in T.  Unlike Alg. 5, equal (v, t) pairs are not merged through a map:
+// T then holds one entry per spilling diagonal, which bounds it by the spill count
+// and gives the same walk.
+__device__ __forceinline__ uint32_t push_trace(const Slab<true> &s, Sh &sh, uint32_t v, uint32_t t) {
+    const uint32_t idx = atomicAdd(&sh.tlen, 1u);
+    if (idx >= 2 * s.cap || idx >= kNoTrace) {
+        set_err(sh, GWFA_ERR_CAPACITY);
+        return kNoTrace;
+    }
+    __stcg(&s.trace[idx], make_uint2(v, t));
+    return idx;
+}
+
 // One extension round over `list` in pruning mode.  Spills are recorded, not
 // applied: apply_spill_requests runs after the round's barrier, so a spill can
 // never touch a diagonal that was present before the round (Alg. 2's presence
 // test) and same-round spills into one diagonal merge by the larger walk base.
 __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &sh, const QCtx &q,
                                    const LEnt *list, uint32_t n_list, int par, uint32_t *req_count,
-                                   uint32_t *claim) {
+                                   uint32_t *claim, bool traceback) {
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     for (;;) {
@@ -402,11 +421,16 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
             const int j2 = j + lcp(q, i, g.words + vi.x, j, (int)vi.y);
             val = pk(j2, kTagSettled, pbase(val));
             __stcg(&s.slots[ent.slot].vals[ln], val);
-            if (ent.v == q.ve && k == q.ke && (uint32_t)j2 == vi.y) sh.found = 1;
+            if (ent.v == q.ve && k == q.ke && (uint32_t)j2 == vi.y) {
+                sh.found = 1;
+                sh.end_payload = pbase(val);
+            }
             a = (unsigned long long)(k + j2) + pbase(val) + (unsigned)j2;   // a = i + W~ (Alg. 4)
             if ((uint32_t)j2 == vi.y) {
-                const uint32_t nb = pbase(val) + vi.y;
-                if (nb > kBaseMask) set_err(sh, GWFA_ERR_CAPACITY);
+                // payload of the spilled diagonals: the walk base (pruning) or the
+                // index of the T entry "left v with this trace" (traceback)
+                const uint32_t nb = traceback ? push_trace(s, sh, ent.v, pbase(val)) : pbase(val) + vi.y;
+                if (!traceback && nb > kBaseMask) set_err(sh, GWFA_ERR_CAPACITY);
                 const uint32_t r = atomicAdd(req_count, 1u);
                 if (r < s.cap) __stcg(&s.req[r], make_int4(k + (int)vi.y, (int)nb, (int)vi.z, (int)vi.w));
                 else set_err(sh, GWFA_ERR_CAPACITY);
@@ -597,10 +621,12 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         sh.peak = 0;
         sh.nq[0] = sh.nq[1] = 0;
         sh.claim[0] = sh.claim[1] = sh.claim[2] = 0;
+        sh.tlen = 0;
+        sh.end_payload = kNoTrace;
         const int slot = find_or_insert(s, sh, tile_key(vs, 0));
         if (slot >= 0) {
             typename VT<P>::T v0;
-            if constexpr (P) v0 = pk(0, kTagFresh, 0);
+            if constexpr (P) v0 = pk(0, kTagFresh, A.traceback ? kNoTrace : 0u);
             else v0 = 0;
             s.slots[slot].vals[0] = v0;
             sh.visited = 1;
@@ -652,7 +678,8 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             uint32_t *claim = &sh.claim[cstep % 3];
             ++cstep;
             if constexpr (P) {
-                extend_round_prune(g, s, sh, q, list, n_list, phase & 1, &sh.nreq[round & 1], claim);
+                extend_round_prune(g, s, sh, q, list, n_list, phase & 1, &sh.nreq[round & 1], claim,
+                                   A.traceback != 0);
                 __syncthreads();
                 if (threadIdx.x == 0) sh.nreq[(round + 1) & 1] = 0;
                 apply_spill_requests(g, s, sh, sh.nreq[round & 1], next_phase & 1, next_list,
@@ -723,6 +750,22 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             r.peak_frontier = sh.peak;
             r.pruned = sh.pruned;
             r.spills = sh.spills;
+            if constexpr (P) {
+                if (A.traceback && status == 0) {
+                    // GwfTraceback (Alg. 6): push the end vertex, then follow T back to the
+                    // start and write the walk in order
+                    const uint32_t te = push_trace(s, sh, q.ve, sh.end_payload);
+                    uint32_t len = 0;
+                    for (uint32_t t = te; t != kNoTrace && len <= sh.tlen; t = __ldcg(&s.trace[t]).y) ++len;
+                    if (A.path_len) A.path_len[qid] = len;
+                    uint32_t pos = len;
+                    for (uint32_t t = te; t != kNoTrace && pos > 0; t = __ldcg(&s.trace[t]).y) {
+                        --pos;
+                        if (A.paths && pos < A.path_cap)
+                            A.paths[(uint64_t)qid * A.path_cap + pos] = __ldcg(&s.trace[t]).x;
+                    }
+                }
+            }
             r.device_us = (uint32_t)min((globaltimer_ns() - t_start) / 1000ull, 0xFFFFFFFFull);
             A.out[qid] = r;
             if (A.stats) {
