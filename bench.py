@@ -138,7 +138,8 @@ def learned_schedule(gw, graph, qs, ref, stream, flush, args) -> dict:
     model = gw.CostModel(graph, seed=1)
     t0 = time.perf_counter()
     eng0 = gw.Engine(graph)
-    feat, tgt, _ = costmodel.collect(model, eng0, train_q)
+    feat, tgt, train_res = costmodel.collect(model, eng0, train_q)
+    coeffs = costmodel.time_coeffs(train_res)
     eng0.close()
     costmodel.fit(model, feat, tgt, steps=1500, batch=512, lr=3e-3)
     t_train = time.perf_counter() - t0
@@ -146,13 +147,15 @@ def learned_schedule(gw, graph, qs, ref, stream, flush, args) -> dict:
     # large-slab CTAs for the queries predicted to overflow tier 0; only as many are
     # launched as there are such queries, so tier 0 keeps the whole GPU otherwise
     cfg.wide.ctas, cfg.wide.log2_tiles, cfg.wide.threads = 152, 19, 512
-    eng = gw.Engine(graph, config=cfg)
     with torch.cuda.stream(stream):
         b = gw.DeviceBatch(qs, stream=stream)
         feat = model.features(b, stream=stream)
         pred = model.predict(feat, stream=stream)
     stream.synchronize()
-    order, n_wide = gw.plan_schedule(pred.cpu().numpy(), int(0.75 * (1 << cfg.tiers[0].log2_tiles)))
+    pred_np = pred.cpu().numpy()
+    order, n_wide = gw.plan_schedule(pred_np, int(0.75 * (1 << cfg.tiers[0].log2_tiles)))
+    cfg.wide.ctas = max(1, costmodel.wide_ctas(pred_np, order, n_wide, cfg.tiers[0].ctas, coeffs))
+    eng = gw.Engine(graph, config=cfg)
     with torch.cuda.stream(stream):
         b2 = gw.DeviceBatch(qs, order=order, stream=stream)
     ts = []
@@ -172,7 +175,6 @@ def learned_schedule(gw, graph, qs, ref, stream, flush, args) -> dict:
     retries = int(eng.last_retries()[0])
     t = float(np.mean(ts))
     ok = r["status"] == 0
-    pred_np = pred.cpu().numpy()
     eng.close()
     return {"value": int(qs.lengths()[ok].sum()) / t / 1e9, "unit": UNIT, "ms_per_step": t * 1e3,
             "n_wide": n_wide, "tier0_overflows": retries, "train_s": t_train,

@@ -344,8 +344,9 @@ int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, ui
  * 2^log2_big); a request enters the class its predicted hash memory fits (the
  * attached cost model, else length > big_length), and a request that overflows
  * a small slab is re-queued into the large class automatically.  The kernel's
- * CTAs leave after idle_us without work (every device wait is bounded) and the
- * next submit or poll starts it again.  Results are identical to gwfa_align.
+ * CTAs leave together once all of them have been idle for idle_us (and in any
+ * case after 16 x idle_us idle; every device wait is bounded), and the next
+ * submit or poll starts it again.  Results are identical to gwfa_align.
  * Thread-safe (one internal lock).
  */
 typedef struct gwfa_server gwfa_server;

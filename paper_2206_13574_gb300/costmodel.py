@@ -86,6 +86,37 @@ def plan(model: CostModel, batch: DeviceBatch, engine: Engine):
     return plan_schedule(pred, tier0)
 
 
+def time_coeffs(results: np.ndarray) -> tuple[float, float]:
+    """Least-squares fit of a query's CTA time: t_us ~ a * scores + b * cells (both >= 0).
+    The per-score term is the latency of one score's phases, the per-cell term the
+    work; their ratio decides how many CTAs a set of queries needs."""
+    ok = results["status"] == 0
+    A = np.stack([results["n_scores"][ok].astype(np.float64), results["cells"][ok].astype(np.float64)], 1)
+    y = results["device_us"][ok].astype(np.float64)
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    return float(max(coef[0], 0.0)), float(max(coef[1], 0.0))
+
+
+def predicted_time(pred: np.ndarray, coeffs: tuple[float, float] | None) -> np.ndarray:
+    d = np.expm1(pred[:, 0].astype(np.float64))
+    cells = np.expm1(pred[:, 3].astype(np.float64))
+    if coeffs is None:
+        return cells
+    return coeffs[0] * (d + 1.0) + coeffs[1] * cells
+
+
+def wide_ctas(pred: np.ndarray, order: np.ndarray, n_wide: int, total_ctas: int,
+              coeffs: tuple[float, float] | None = None) -> int:
+    """CTAs for the large-slab class: its share of the predicted CTA time (or of the
+    predicted cells without time coefficients) times the CTAs that fit on the GPU,
+    at least one, at most one per wide query."""
+    if n_wide == 0:
+        return 0
+    t = predicted_time(pred, coeffs)
+    share = t[order[:n_wide]].sum() / max(t.sum(), 1e-9)
+    return int(min(n_wide, max(1, round(total_ctas * share))))
+
+
 def spearman(a: np.ndarray, b: np.ndarray) -> float:
     ra = np.argsort(np.argsort(a)).astype(np.float64)
     rb = np.argsort(np.argsort(b)).astype(np.float64)
@@ -93,4 +124,4 @@ def spearman(a: np.ndarray, b: np.ndarray) -> float:
 
 
 __all__ = ["collect", "fit", "plan", "r2", "save", "load_into", "transfer", "targets_of", "spearman",
-           "MODEL_TARGETS", "Graph"]
+           "time_coeffs", "predicted_time", "wide_ctas", "MODEL_TARGETS", "Graph"]

@@ -137,7 +137,9 @@ struct ServerArgs {
     const unsigned long long *tail[2];
     unsigned long long *head;      // device, per class
     const unsigned long long *stop;
-    unsigned long long *timeouts;  // device: CTAs that left after wait_limit idle polls
+    unsigned long long *timeouts;  // device: CTAs that left after an idle period
+    unsigned int *idle_votes;      // device: CTAs currently idle for wait_limit polls or more
+    uint32_t n_ctas;
     uint32_t ring, slot_words;
     uint32_t wait_limit, sleep_ns;
     int32_t max_lag, max_score;

@@ -815,8 +815,10 @@ __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned l
 // Serving: a persistent kernel whose CTAs take requests from host-published rings
 // (continuous batching: a CTA starts a new request as soon as it finishes one).
 // CTAs [0, n_small) serve class 0 (small hash slabs), the rest class 1.  Every
-// wait is bounded: a CTA that finds no request for wait_limit polls (or sees the
-// stop flag) leaves the loop, and the host relaunches the kernel when work comes.
+// wait is bounded: a CTA idle for wait_limit polls votes idle (and withdraws the
+// vote if work comes); the CTAs leave together once every CTA has voted, or after
+// 16 x wait_limit polls in any case, and the host relaunches the kernel when work
+// comes.  Leaving together keeps the full set of CTAs whenever the kernel runs.
 template <bool P>
 __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
     extern __shared__ uint32_t qsm[];   // the request's packed words, staged
@@ -833,11 +835,17 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
         if (threadIdx.x == 0) {
             int go = 0;
             uint32_t polls = 0;
+            bool voted = false;
             for (;;) {
                 if (ld_acquire_sys(S.stop)) break;
                 const unsigned long long h = atomicAdd(S.head + cls, 0ull);
                 const unsigned long long t = ld_acquire_sys(S.tail[cls]);
                 if (h < t) {
+                    if (voted) {
+                        atomicSub(S.idle_votes, 1u);
+                        voted = false;
+                    }
+                    polls = 0;
                     if (atomicCAS(S.head + cls, h, h + 1) == h) {
                         s_ticket = h;
                         go = 1;
@@ -845,7 +853,12 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
                     }
                     continue;
                 }
-                if (++polls > S.wait_limit) {
+                ++polls;
+                if (!voted && polls > S.wait_limit) {
+                    atomicAdd(S.idle_votes, 1u);
+                    voted = true;
+                }
+                if (voted && (atomicAdd(S.idle_votes, 0u) >= S.n_ctas || polls > 16u * S.wait_limit)) {
                     atomicAdd(S.timeouts, 1ull);
                     break;
                 }

@@ -57,6 +57,7 @@ struct gwfa_server {
     unsigned long long *tail[2] = {};
     unsigned long long *stop = nullptr;
     unsigned long long *d_head = nullptr, *d_timeouts = nullptr;
+    unsigned int *d_votes = nullptr;
     gwfa::ServerArgs args{};
     uint32_t slot_words = 0, smem_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -86,7 +87,9 @@ int ensure_running(gwfa_server *sv) {
         if (q != cudaSuccess) return sstat(q);
     }
     const uint32_t ctas = sv->cfg.ctas_small + sv->cfg.ctas_big;
-    int st = sstat(gwfa::launch_server(sv->args, sv->prune, ctas, sv->cfg.threads, sv->smem_bytes, sv->stream));
+    // a new generation of CTAs starts with no idle votes (stream-ordered after the last)
+    int st = sstat(cudaMemsetAsync(sv->d_votes, 0, sizeof(unsigned int), sv->stream));
+    if (!st) st = sstat(gwfa::launch_server(sv->args, sv->prune, ctas, sv->cfg.threads, sv->smem_bytes, sv->stream));
     if (!st) {
         sv->launched = true;
         sv->n_launches++;
@@ -194,6 +197,7 @@ int gwfa_server_create(const gwfa_graph *g, const gwfa_server_config *cfg, const
                                           c.log2_big, sv->prune, sv->stream));
     if (!st) st = sstat(cudaMalloc(&sv->d_head, 2 * sizeof(unsigned long long)));
     if (!st) st = sstat(cudaMalloc(&sv->d_timeouts, sizeof(unsigned long long)));
+    if (!st) st = sstat(cudaMalloc(&sv->d_votes, sizeof(unsigned int)));
     if (!st) st = sstat(cudaMemsetAsync(sv->d_head, 0, 2 * sizeof(unsigned long long), sv->stream));
     if (!st) st = sstat(cudaMemsetAsync(sv->d_timeouts, 0, sizeof(unsigned long long), sv->stream));
     // pinned, mapped host block
@@ -249,6 +253,8 @@ int gwfa_server_create(const gwfa_graph *g, const gwfa_server_config *cfg, const
     a.stop = (const unsigned long long *)p;
     a.head = sv->d_head;
     a.timeouts = sv->d_timeouts;
+    a.idle_votes = sv->d_votes;
+    a.n_ctas = c.ctas_small + c.ctas_big;
     a.ring = c.ring_slots;
     a.slot_words = sv->slot_words;
     a.sleep_ns = 2000;
@@ -379,6 +385,7 @@ int gwfa_server_destroy(gwfa_server *sv) {
     cudaFree(sv->slabs);
     cudaFree(sv->d_head);
     cudaFree(sv->d_timeouts);
+    cudaFree(sv->d_votes);
     if (sv->host) cudaFreeHost(sv->host);
     delete sv;
     return GWFA_OK;

@@ -1,0 +1,183 @@
+"""Measurements on the workloads beside the benchmark's (run on a GPU).
+
+    python -m paper_2206_13574_gb300.experiments config3     # cyclic graph: exact vs lag-pruned
+    python -m paper_2206_13574_gb300.experiments scheduler   # large graph: learned vs plain scheduling
+    python -m paper_2206_13574_gb300.experiments serving     # server vs one-query-at-a-time
+
+Each prints one JSON line.  Inputs are the seeded synthetic workloads of synth.py.
+"""
+from __future__ import annotations
+
+import json
+import sys
+import time
+
+import numpy as np
+
+
+def _timed_run(engine, batch, reps=1, **kw):
+    import torch
+    st = torch.cuda.current_stream()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        batch.run(engine, **kw)
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return best
+
+
+def config3(n_pruned: int = 2000, n_exact: int = 200, a_diff: int = 1000) -> dict:
+    """Cyclic graph with tandem-repeat loops, 50 kb queries at 8% errors: the lag-pruned
+    distances (upper bounds) against exact ones on a subset, with both timings."""
+    import paper_2206_13574_gb300 as gw
+    from paper_2206_13574_gb300 import synth
+    import torch
+    g, qs = synth.make_config(3, n_queries=n_pruned)
+    graph = gw.Graph.from_synth(g)
+    order = np.argsort(-qs.lengths(), kind="stable").astype(np.uint32)
+    bp = gw.DeviceBatch(qs, order=order)
+    engp = gw.Engine(graph, prune=True)
+    bp.run(engp, max_lag=a_diff)
+    t_pr = _timed_run(engp, bp, max_lag=a_diff)
+    pr = bp.results()
+    engp.close()
+    sub = qs.subset(np.arange(n_exact))
+    be = gw.DeviceBatch(sub)
+    cfg = gw.default_config(graph)
+    cfg.tiers[0].ctas, cfg.tiers[0].log2_tiles = 304, 20
+    cfg.tiers[1].ctas, cfg.tiers[1].log2_tiles = 38, 22
+    cfg.tiers[2].ctas, cfg.tiers[2].log2_tiles = 4, 24
+    enge = gw.Engine(graph, config=cfg)
+    t_ex = _timed_run(enge, be)
+    ex = be.results()
+    enge.close()
+    torch.cuda.synchronize()
+    prs = pr[:n_exact]
+    ok = (ex["status"] == 0) & (prs["status"] == 0)
+    return {"workload": "config3: 1 Mb cyclic graph (tandem-repeat loops), 50 kb queries, 8% errors",
+            "pruned": {"queries": n_pruned, "a_diff": a_diff, "s": t_pr,
+                       "gbp_per_s": float(qs.lengths()[pr["status"] == 0].sum()) / t_pr / 1e9,
+                       "cells": int(pr["cells"].sum()), "upper_bound_rate": float(pr["is_upper_bound"].mean()),
+                       "ok": int((pr["status"] == 0).sum())},
+            "exact": {"queries": n_exact, "s": t_ex,
+                      "gbp_per_s": float(sub.lengths()[ex["status"] == 0].sum()) / t_ex / 1e9,
+                      "cells": int(ex["cells"].sum()), "ok": int((ex["status"] == 0).sum()),
+                      "mean_distance": float(ex["edit_distance"][ex["status"] == 0].mean())},
+            "exact_match_rate": float((prs["edit_distance"][ok] == ex["edit_distance"][ok]).mean()),
+            "pruned_never_below_exact": bool(np.all(prs["edit_distance"][ok] >= ex["edit_distance"][ok])),
+            "work_ratio_exact_over_pruned": float(ex["cells"][ok].sum() / max(prs["cells"][ok].sum(), 1))}
+
+
+def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300) -> dict:
+    """Large graph (50 Mb, lognormal 1-100 kb queries, 0.1-10% divergence), exact:
+    plain schedules (input order, longest first) against the learned plan of a cost
+    model trained on config-2 and config-3-graph logs (other graphs)."""
+    import paper_2206_13574_gb300 as gw
+    from paper_2206_13574_gb300 import costmodel, synth
+    import torch
+    # training logs on the two other graphs
+    g2, q2 = synth.make_config(2, n_queries=n_train_c2, seed=12)
+    c3 = synth.CONFIGS[3]
+    g3 = synth.make_graph(c3["graph"], 3)
+    q3 = synth.make_queries(g3, n_train_c3, 13, lambda r: r.one_int(3000, 15000), lambda r: 0.005 + 0.05 * r.one(),
+                            c3["weights"], c3["loops"])
+    feats, tgts = [], []
+    gr2 = gw.Graph.from_synth(g2)
+    m2 = gw.CostModel(gr2, seed=1)
+    f, t, r2res = costmodel.collect(m2, gw.Engine(gr2), q2)
+    feats.append(f)
+    tgts.append(t)
+    coeffs = costmodel.time_coeffs(r2res)
+    gr3 = gw.Graph.from_synth(g3)
+    m3 = gw.CostModel(gr3, seed=1)
+    cfg3 = gw.default_config(gr3)
+    cfg3.tiers[1].log2_tiles, cfg3.tiers[2].log2_tiles = 20, 23
+    f, t, _ = costmodel.collect(m3, gw.Engine(gr3, config=cfg3), q3)
+    feats.append(f)
+    tgts.append(t)
+    feat = torch.cat(feats)
+    tgt = torch.cat(tgts)
+    costmodel.fit(m2, feat, tgt, steps=2000, batch=512, lr=3e-3)
+    # the large workload
+    g4, q4 = synth.make_config(4, n_queries=n)
+    gr4 = gw.Graph.from_synth(g4)
+    m4 = gw.CostModel(gr4, seed=1)
+    costmodel.transfer(m2, m4)
+    b0 = gw.DeviceBatch(q4)
+    pred = m4.predict(m4.features(b0)).cpu().numpy()
+    base = gw.default_config(gr4)
+    total = base.tiers[0].ctas
+    l_order, l_wide = gw.plan_schedule(pred, int(0.75 * (1 << base.tiers[0].log2_tiles)))
+    w_ctas = costmodel.wide_ctas(pred, l_order, l_wide, total, coeffs)
+
+    def engine(wide: int):
+        cfg = gw.default_config(gr4)
+        cfg.tiers[1].ctas, cfg.tiers[1].log2_tiles = 152, 20
+        cfg.tiers[2].ctas, cfg.tiers[2].log2_tiles = 19, 23
+        cfg.wide.ctas, cfg.wide.log2_tiles, cfg.wide.threads = wide, 20, 512
+        return gw.Engine(gr4, config=cfg)
+
+    out = {"workload": f"config4: 50 Mb graph, {n} lognormal 1-100 kb queries, 0.1-10% divergence, exact",
+           "train": f"{len(q2)} config-2 + {len(q3)} config-3-graph queries, 2000 Adam steps",
+           "learned_wide_ctas": w_ctas, "time_coeffs_us": list(coeffs)}
+    ref = None
+    plans = {"plain_fifo": (None, 0, 0), "plain_longest_first": (np.argsort(-q4.lengths(), kind="stable"), 0, 0),
+             "learned": (l_order, l_wide, w_ctas)}
+    for name, (order, nw, wc) in plans.items():
+        eng = engine(wc)
+        b = gw.DeviceBatch(q4, order=None if order is None else np.asarray(order, np.uint32))
+        b.run(eng, n_wide=nw)
+        t = _timed_run(eng, b, n_wide=nw)
+        r = b.results()
+        retries = eng.last_retries()
+        if ref is None:
+            ref = r
+        assert np.array_equal(r["edit_distance"], ref["edit_distance"])
+        out[name] = {"s": t, "gbp_per_s": float(q4.lengths()[r["status"] == 0].sum()) / t / 1e9,
+                     "tier0_overflows": int(retries[0]), "tier1_overflows": int(retries[1]), "n_wide": int(nw),
+                     "ok": int((r["status"] == 0).sum()), "slab_bytes": eng.device_bytes}
+        eng.close()
+    out["cells"] = int(ref["cells"].sum())
+    out["spearman_pred_cells"] = costmodel.spearman(pred[:, 3], np.log1p(ref["cells"].astype(np.float64)))
+    out["r2_log_cells"] = float(costmodel.r2(pred[:, 3:4], np.log1p(ref["cells"].astype(np.float64))[:, None])[0])
+    return out
+
+
+def serving(n_pool: int = 3000, rates=(1000.0, 5000.0, 20000.0), duration: float = 1.0,
+            plain_rate: float = 100.0, plain_duration: float = 2.0) -> dict:
+    """Config-2 graph resident, Poisson arrivals: the continuous-batching server's
+    p50/p99 at several rates, and the plain one-query-at-a-time path at a low rate."""
+    import paper_2206_13574_gb300 as gw
+    from paper_2206_13574_gb300 import serving as sv
+    from paper_2206_13574_gb300 import synth
+    g, qs = synth.make_config(2, n_queries=n_pool)
+    graph = gw.Graph.from_synth(g)
+    srv = gw.Server(graph)
+    out = {"workload": "config2 graph, config-2 queries, Poisson arrivals"}
+    for lam in rates:
+        arr = synth.poisson_arrivals(lam, duration, seed=int(lam))
+        idx = np.arange(len(arr)) % n_pool
+        out[f"server_lambda_{int(lam)}"], _ = sv.run_server(srv, qs, arr, idx)
+    out["server_stats"] = srv.stats()
+    srv.close()
+    arr = synth.poisson_arrivals(plain_rate, plain_duration, seed=3)
+    idx = np.arange(len(arr)) % n_pool
+    out[f"plain_lambda_{int(plain_rate)}"], _ = sv.run_plain(graph, qs, arr, idx)
+    srv2 = gw.Server(graph)
+    out[f"server_lambda_{int(plain_rate)}"], _ = sv.run_server(srv2, qs, arr, idx)
+    srv2.close()
+    return out
+
+
+if __name__ == "__main__":
+    import paper_2206_13574_gb300._build as b
+    b.build()
+    which = sys.argv[1] if len(sys.argv) > 1 else "config3"
+    t0 = time.time()
+    res = {"config3": config3, "scheduler": scheduler, "serving": serving}[which]()
+    res["wall_s"] = time.time() - t0
+    print(json.dumps(res))
