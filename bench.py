@@ -153,7 +153,7 @@ def learned_schedule(gw, graph, qs, ref, stream, flush, args) -> dict:
         pred = model.predict(feat, stream=stream)
     stream.synchronize()
     pred_np = pred.cpu().numpy()
-    order, n_wide = gw.plan_schedule(pred_np, int(0.75 * (1 << cfg.tiers[0].log2_tiles)))
+    order, _, n_wide = gw.plan_schedule(pred_np, *costmodel.capacities(cfg))
     cfg.wide.ctas = max(1, costmodel.wide_ctas(pred_np, order, n_wide, cfg.tiers[0].ctas, coeffs))
     eng = gw.Engine(graph, config=cfg)
     with torch.cuda.stream(stream):
@@ -353,7 +353,8 @@ def main():
 
     def e2e_step():
         st = lib.gwfa_align_batch(eng.handle, len(qs), h_q.data_ptr(), h_off.data_ptr(), h_vs.data_ptr(),
-                                  h_ve.data_ptr(), h_order.data_ptr(), n_wide, ctypes.byref(opts),
+                                  h_ve.data_ptr(), h_order.data_ptr(), gw._sched(0, n_wide),
+                                  ctypes.byref(opts),
                                   h_out.data_ptr(), stream.cuda_stream)
         assert st == 0, st
 

@@ -150,9 +150,11 @@ typedef struct gwfa_engine gwfa_engine;
  *   tiers[t].ctas  CTAs of tier t
  *   tiers[t].log2_tiles  slab capacity in 8-diagonal tiles (log2)
  *   tiers[t].threads     threads per CTA of tier t (0 = `threads`)
- *   wide           an extra set of (typically 512-thread) CTAs that runs concurrently
- *                  with tier 0 on the first n_wide queries of the schedule, so that
- *                  the heaviest queries do not form a tail behind narrow CTAs
+ *   huge, wide     two extra classes of CTAs (usually with larger slabs) that run
+ *                  concurrently with tier 0 on the first n_huge, then the next
+ *                  n_wide queries of the schedule (gwfa_schedule), so the heaviest
+ *                  queries start at once on slabs that fit them instead of forming a
+ *                  tail of overflow re-runs; their overflows go to the retry tiers
  *   threads        threads per CTA (multiple of 32, 64..512); 0 = 128
  *   max_queries, max_bases  sizes of the engine's staging buffers for the
  *                  host-buffer entry point (grown on demand)
@@ -168,14 +170,22 @@ typedef struct {
 typedef struct {
     uint32_t n_tiers;
     gwfa_tier tiers[GWFA_MAX_TIERS];
-    gwfa_tier wide;           /* CTAs for the heaviest queries, run beside tier 0; ctas 0 = none */
+    gwfa_tier wide;           /* CTAs for heavy queries, run beside tier 0; ctas 0 = none */
+    gwfa_tier huge;           /* CTAs with very large slabs for the heaviest, beside tier 0 */
     uint32_t threads;
     uint32_t prune_slabs;     /* 1: size slabs for pruning mode (64-bit offsets) */
     uint64_t max_queries;
     uint64_t max_bases;
 } gwfa_engine_config;
 
-/* fills a default configuration for this GPU (3 tiers, 128 threads) */
+/* Placement of a batch: queue positions [0, n_huge) run on the huge class,
+ * [n_huge, n_huge + n_wide) on the wide class, the rest on tier 0. */
+typedef struct {
+    uint32_t n_huge;
+    uint32_t n_wide;
+} gwfa_schedule;
+
+/* fills a default configuration for this GPU (3 tiers, 512 threads, no classes) */
 int gwfa_engine_default_config(const gwfa_graph *g, int prune, gwfa_engine_config *cfg);
 int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_engine **out);
 int gwfa_engine_destroy(gwfa_engine *e);
@@ -186,8 +196,8 @@ uint64_t gwfa_engine_device_bytes(const gwfa_engine *e);
  * Host-buffer batch (end to end).  Queries concatenated in h_q (ASCII) with
  * h_q_off[n_queries+1] byte offsets, per-query start/end vertices in
  * h_v_s / h_v_e.  h_order (may be NULL = input order) is the order in which the
- * work queue hands queries to CTAs (a permutation of 0..n_queries-1); its first
- * n_wide entries go to the engine's wide CTAs (0 = none).  The call
+ * work queue hands queries to CTAs (a permutation of 0..n_queries-1), placed by
+ * `sched` (NULL = all on tier 0).  The call
  * copies the inputs to the device, packs them (kernel), runs the tiers, copies
  * the n_queries results to h_out and returns when they are there.  Per-query
  * errors are in h_out[i].status; the return value is the first fatal error.
@@ -195,7 +205,8 @@ uint64_t gwfa_engine_device_bytes(const gwfa_engine *e);
  */
 int gwfa_align_batch(gwfa_engine *e, uint32_t n_queries, const char *h_q, const uint64_t *h_q_off,
                      const uint32_t *h_v_s, const uint32_t *h_v_e, const uint32_t *h_order,
-                     uint32_t n_wide, const gwfa_opts *opts, gwfa_result *h_out, void *stream);
+                     const gwfa_schedule *sched, const gwfa_opts *opts, gwfa_result *h_out,
+                     void *stream);
 
 /*
  * Device-resident packing of queries (the step gwfa_align_batch runs after its
@@ -211,14 +222,15 @@ int gwfa_pack_queries_device(uint32_t n_queries, const char *d_q, const uint64_t
  * Device-resident batch (inputs already in HBM): d_words / d_q_off as written
  * by gwfa_pack_queries_device (d_status may be NULL, else queries with a
  * nonzero status are skipped and keep it), d_v_s / d_v_e start/end vertices,
- * d_order the queue order (NULL = 0..n-1) whose first n_wide entries go to the
- * wide CTAs, results into d_out[n_queries].
+ * d_order the queue order (NULL = 0..n-1) placed by `sched` (NULL = all on
+ * tier 0; host memory), results into d_out[n_queries].
  * Asynchronous on `stream`; no host synchronisation inside.
  */
 int gwfa_align_batch_device(gwfa_engine *e, uint32_t n_queries, const uint32_t *d_words,
                             const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
-                            const uint32_t *d_order, uint32_t n_wide, const int32_t *d_status,
-                            const gwfa_opts *opts, gwfa_result *d_out, void *stream);
+                            const uint32_t *d_order, const gwfa_schedule *sched,
+                            const int32_t *d_status, const gwfa_opts *opts, gwfa_result *d_out,
+                            void *stream);
 
 /*
  * Allocation-free batch alignment (no counterpart in the paper: it exists for
@@ -324,15 +336,16 @@ int gwfa_model_predict_host(const gwfa_model *m, const char *h_q, uint32_t n, ui
                             uint32_t v_e, float *h_pred);
 
 /*
- * Batch plan from predicted costs (host, no GPU): h_order gets the queries by
- * decreasing predicted cells (longest processing time first); the queries whose
- * predicted hash tiles exceed `tier0_tiles` are moved to the front and counted in
- * *n_wide, so they start on the engine's wide (large-slab) CTAs instead of
- * overflowing tier 0 and being re-run.
+ * Batch plan from predicted costs (host, no GPU): the queries whose predicted hash
+ * tiles exceed `wide_tiles` (0 = no huge class) come first (out->n_huge), then
+ * those exceeding `tier0_tiles` (out->n_wide), then the rest, each group by
+ * decreasing predicted cells (longest processing time first), so the heavy
+ * queries start at once on slabs that fit them instead of overflowing tier 0 and
+ * being re-run.
  *   h_pred  n x 4 predictions (log1p units, as from gwfa_model_predict_device)
  */
-int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, uint32_t *h_order,
-                       uint32_t *n_wide);
+int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, uint64_t wide_tiles,
+                       uint32_t *h_order, gwfa_schedule *out);
 
 /* ---- serving: continuous batching over a resident graph ----------------- */
 /*

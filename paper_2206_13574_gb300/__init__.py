@@ -66,8 +66,17 @@ class gwfa_tier(ctypes.Structure):
 
 class gwfa_engine_config(ctypes.Structure):
     _fields_ = [("n_tiers", ctypes.c_uint32), ("tiers", gwfa_tier * GWFA_MAX_TIERS),
-                ("wide", gwfa_tier), ("threads", ctypes.c_uint32), ("prune_slabs", ctypes.c_uint32),
+                ("wide", gwfa_tier), ("huge", gwfa_tier), ("threads", ctypes.c_uint32),
+                ("prune_slabs", ctypes.c_uint32),
                 ("max_queries", ctypes.c_uint64), ("max_bases", ctypes.c_uint64)]
+
+
+class gwfa_schedule(ctypes.Structure):
+    _fields_ = [("n_huge", ctypes.c_uint32), ("n_wide", ctypes.c_uint32)]
+
+
+def _sched(n_huge: int, n_wide: int):
+    return ctypes.byref(gwfa_schedule(int(n_huge), int(n_wide))) if (n_huge or n_wide) else None
 
 
 # every symbol include/gwfa.h declares, with its ctypes signature
@@ -84,10 +93,10 @@ SIGNATURES = {
     "gwfa_engine_create": ([_P, ctypes.POINTER(gwfa_engine_config), ctypes.POINTER(_P)], ctypes.c_int),
     "gwfa_engine_destroy": ([_P], ctypes.c_int),
     "gwfa_engine_device_bytes": ([_P], _u64),
-    "gwfa_align_batch": ([_P, _u32, _P, _P, _P, _P, _P, _u32, ctypes.POINTER(gwfa_opts), _P, _P],
+    "gwfa_align_batch": ([_P, _u32, _P, _P, _P, _P, _P, _P, ctypes.POINTER(gwfa_opts), _P, _P],
                          ctypes.c_int),
     "gwfa_pack_queries_device": ([_u32, _P, _P, _P, _P, _P], ctypes.c_int),
-    "gwfa_align_batch_device": ([_P, _u32, _P, _P, _P, _P, _P, _u32, _P, ctypes.POINTER(gwfa_opts), _P,
+    "gwfa_align_batch_device": ([_P, _u32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(gwfa_opts), _P,
                                  _P], ctypes.c_int),
     "gwfa_engine_last_launches": ([_P], _u32),
     "gwfa_engine_set_stats": ([_P, _P], ctypes.c_int),
@@ -104,7 +113,7 @@ SIGNATURES.update({
     "gwfa_model_gradient_device": ([_P, _u32, _P, _P, _P, _P, _P], ctypes.c_int),
     "gwfa_model_train_device": ([_P, _u32, _P, _P, _u32, _u32, ctypes.c_float, _u64, _P, _P],
                                 ctypes.c_int),
-    "gwfa_plan_schedule": ([_u32, _P, _u64, _P, _P], ctypes.c_int),
+    "gwfa_plan_schedule": ([_u32, _P, _u64, _u64, _P, _P], ctypes.c_int),
 })
 
 
@@ -287,7 +296,8 @@ class Engine:
         _check(load().gwfa_engine_set_stats(self.handle, d_stats or None), "gwfa_engine_set_stats")
 
     def align_batch(self, seq, off, v_s, v_e, order=None, max_lag: int = 0, max_score: int = -1,
-                    stream: int = 0, out: np.ndarray | None = None, n_wide: int = 0) -> np.ndarray:
+                    stream: int = 0, out: np.ndarray | None = None, n_wide: int = 0,
+                    n_huge: int = 0) -> np.ndarray:
         """Host buffers in, host results out (gwfa_align_batch)."""
         seq = _c(seq, np.uint8)
         off = _c(off, np.uint64)
@@ -298,7 +308,8 @@ class Engine:
         o = _opts(max_lag, max_score)
         od = None if order is None else _c(order, np.uint32)
         _check(load().gwfa_align_batch(self.handle, n, seq.ctypes.data, off.ctypes.data, vs.ctypes.data,
-                                       ve.ctypes.data, None if od is None else od.ctypes.data, n_wide,
+                                       ve.ctypes.data, None if od is None else od.ctypes.data,
+                                       _sched(n_huge, n_wide),
                                        ctypes.byref(o), res.ctypes.data, stream or None),
                "gwfa_align_batch")
         return res
@@ -306,11 +317,12 @@ class Engine:
     def align_batch_device(self, n: int, d_words: int, d_q_off: int, d_v_s: int, d_v_e: int,
                            d_order: int | None, d_status: int | None, d_out: int,
                            max_lag: int = 0, max_score: int = -1, stream: int = 0, n_wide: int = 0,
-                           traceback: bool = False):
+                           traceback: bool = False, n_huge: int = 0):
         """Device pointers in and out, asynchronous on `stream` (gwfa_align_batch_device)."""
         o = _opts(max_lag, max_score, int(traceback))
         _check(load().gwfa_align_batch_device(self.handle, n, d_words, d_q_off, d_v_s, d_v_e,
-                                              d_order or None, n_wide, d_status or None, ctypes.byref(o),
+                                              d_order or None, _sched(n_huge, n_wide), d_status or None,
+                                              ctypes.byref(o),
                                               d_out, stream or None),
                "gwfa_align_batch_device")
 
@@ -359,14 +371,14 @@ class DeviceBatch:
                             self.status.data_ptr(), st.cuda_stream)
 
     def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None, n_wide: int = 0,
-            traceback: bool = False):
+            traceback: bool = False, n_huge: int = 0):
         import torch
         st = stream if stream is not None else torch.cuda.current_stream(self.q.device)
         engine.align_batch_device(self.n, self.words.data_ptr(), self.q_off.data_ptr(),
                                   self.v_s.data_ptr(), self.v_e.data_ptr(),
                                   None if self.order is None else self.order.data_ptr(),
                                   self.status.data_ptr(), self.out.data_ptr(), max_lag, max_score,
-                                  st.cuda_stream, n_wide, traceback)
+                                  st.cuda_stream, n_wide, traceback, n_huge)
 
     def results(self) -> np.ndarray:
         return self.out.cpu().numpy().view(RESULT_DTYPE)
@@ -449,15 +461,15 @@ class CostModel:
             pass
 
 
-def plan_schedule(pred: np.ndarray, tier0_tiles: int):
-    """(order, n_wide) from predictions (n x 4, log1p units): gwfa_plan_schedule."""
+def plan_schedule(pred: np.ndarray, tier0_tiles: int, wide_tiles: int = 0):
+    """(order, n_huge, n_wide) from predictions (n x 4, log1p units): gwfa_plan_schedule."""
     pred = _c(pred, np.float32)
     n = pred.shape[0]
     order = np.zeros(n, dtype=np.uint32)
-    nw = ctypes.c_uint32()
-    _check(load().gwfa_plan_schedule(n, pred.ctypes.data, int(tier0_tiles), order.ctypes.data,
-                                     ctypes.byref(nw)), "gwfa_plan_schedule")
-    return order, int(nw.value)
+    sc = gwfa_schedule()
+    _check(load().gwfa_plan_schedule(n, pred.ctypes.data, int(tier0_tiles), int(wide_tiles),
+                                     order.ctypes.data, ctypes.byref(sc)), "gwfa_plan_schedule")
+    return order, int(sc.n_huge), int(sc.n_wide)
 
 
 class Server:

@@ -7,10 +7,10 @@ kernels (gwfa_model_*); this module only moves tensors between those calls:
   and the targets log1p(edit distance, peak |Q|, visited diagonals, cells) --
   the work counters the alignment kernels report;
 * fit(): set the normalisation from the training set, then train on the GPU;
-* plan(): predictions -> (order, n_wide) for gwfa_align_batch[_device]: longest
-  predicted work first, predicted hash overflows straight onto the large-slab
-  (wide) CTAs.  The plain scheduler is the input order or length order, with
-  every query starting in tier 0.
+* plan(): predictions -> (order, n_huge, n_wide) for gwfa_align_batch[_device]:
+  longest predicted work first, predicted hash overflows straight onto the
+  large-slab classes (huge, wide) that run beside tier 0.  The plain scheduler is
+  the input order or length order, with every query starting in tier 0.
 """
 from __future__ import annotations
 
@@ -78,12 +78,19 @@ def load_into(model: CostModel, path: str):
     model.set_normalization(z["fmean"], z["fstd"], z["tmean"], z["tstd"])
 
 
+def capacities(config) -> tuple[int, int]:
+    """(tier-0 tiles, wide-class tiles) a query may fill before it overflows: the
+    hash tables' 0.75 load limit; wide 0 when the engine has no huge class."""
+    tier0 = int(0.75 * (1 << config.tiers[0].log2_tiles))
+    wide = int(0.75 * (1 << config.wide.log2_tiles)) if config.huge.ctas else 0
+    return tier0, wide
+
+
 def plan(model: CostModel, batch: DeviceBatch, engine: Engine):
-    """(order, n_wide) for `batch` from the model's predictions."""
+    """(order, n_huge, n_wide) for `batch` from the model's predictions."""
     from . import plan_schedule
     pred = model.predict(model.features(batch)).cpu().numpy()
-    tier0 = int(0.75 * (1 << engine.config.tiers[0].log2_tiles))
-    return plan_schedule(pred, tier0)
+    return plan_schedule(pred, *capacities(engine.config))
 
 
 def time_coeffs(results: np.ndarray) -> tuple[float, float]:
@@ -106,14 +113,15 @@ def predicted_time(pred: np.ndarray, coeffs: tuple[float, float] | None) -> np.n
 
 
 def wide_ctas(pred: np.ndarray, order: np.ndarray, n_wide: int, total_ctas: int,
-              coeffs: tuple[float, float] | None = None) -> int:
-    """CTAs for the large-slab class: its share of the predicted CTA time (or of the
-    predicted cells without time coefficients) times the CTAs that fit on the GPU,
-    at least one, at most one per wide query."""
+              coeffs: tuple[float, float] | None = None, first: int = 0) -> int:
+    """CTAs for a large-slab class holding queue positions [first, first + n_wide):
+    its share of the predicted CTA time (or of the predicted cells without time
+    coefficients) times the CTAs that fit on the GPU, at least one, at most one per
+    query of the class."""
     if n_wide == 0:
         return 0
     t = predicted_time(pred, coeffs)
-    share = t[order[:n_wide]].sum() / max(t.sum(), 1e-9)
+    share = t[order[first:first + n_wide]].sum() / max(t.sum(), 1e-9)
     return int(min(n_wide, max(1, round(total_ctas * share))))
 
 
@@ -124,4 +132,4 @@ def spearman(a: np.ndarray, b: np.ndarray) -> float:
 
 
 __all__ = ["collect", "fit", "plan", "r2", "save", "load_into", "transfer", "targets_of", "spearman",
-           "time_coeffs", "predicted_time", "wide_ctas", "MODEL_TARGETS", "Graph"]
+           "time_coeffs", "predicted_time", "wide_ctas", "capacities", "MODEL_TARGETS", "Graph"]

@@ -346,7 +346,8 @@ int gwfa_engine_default_config(const gwfa_graph *g, int prune, gwfa_engine_confi
     // of dependent L2 round trips, so resident warps matter more than registers)
     cfg->threads = 512;
     if (gwfa::align_occupancy(prune != 0, cfg->threads, &bps) || bps < 1) bps = 1;
-    cfg->wide = {0u, prune ? 18u : 19u, 512u, 0u};   // no separate wide class by default
+    cfg->wide = {0u, prune ? 18u : 19u, 512u, 0u};   // no concurrent classes by default
+    cfg->huge = {0u, 22u, 512u, 0u};
     cfg->n_tiers = 3;
     cfg->tiers[0] = {(uint32_t)(sms * bps), prune ? 15u : 16u, 0u, 0u};
     cfg->tiers[1] = {(uint32_t)sms, 19u, 0u, 0u};
@@ -362,7 +363,10 @@ int gwfa_engine_destroy(gwfa_engine *e) {
     cudaSetDevice(e->g->device);
     for (int t = 0; t < GWFA_MAX_TIERS; ++t) cudaFree(e->slabs[t]);
     cudaFree(e->wide_slabs);
+    cudaFree(e->huge_slabs);
     if (e->side) cudaStreamDestroy(e->side);
+    if (e->side2) cudaStreamDestroy(e->side2);
+    if (e->ev_join2) cudaEventDestroy(e->ev_join2);
     if (e->ev_fork) cudaEventDestroy(e->ev_fork);
     if (e->ev_join) cudaEventDestroy(e->ev_join);
     cudaFree(e->counters);
@@ -390,9 +394,9 @@ int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_
     if (cfg->n_tiers < 1 || cfg->n_tiers > GWFA_MAX_TIERS) return GWFA_ERR_INVALID;
     const uint32_t threads = cfg->threads ? cfg->threads : 128;
     if (threads % 32 || threads < 64 || threads > 512) return GWFA_ERR_INVALID;
-    for (uint32_t t = 0; t <= cfg->n_tiers; ++t) {
-        const gwfa_tier &tt = t < cfg->n_tiers ? cfg->tiers[t] : cfg->wide;
-        if (t == cfg->n_tiers && tt.ctas == 0) break;   // no wide CTAs
+    for (uint32_t t = 0; t < cfg->n_tiers + 2; ++t) {
+        const gwfa_tier &tt = t < cfg->n_tiers ? cfg->tiers[t] : (t == cfg->n_tiers ? cfg->wide : cfg->huge);
+        if (t >= cfg->n_tiers && tt.ctas == 0) continue;   // class not used
         const uint32_t th = tt.threads;
         if (tt.ctas == 0 || tt.log2_tiles < 8 || tt.log2_tiles > gwfa::kMaxLog2Tiles ||
             (th && (th % 32 || th < 64 || th > 512)))
@@ -416,6 +420,18 @@ int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_
                                                     e->stream));
         e->device_bytes += bytes;
     }
+    if (!st && cfg->huge.ctas) {
+        e->huge_slab_bytes = gwfa::slab_layout(cfg->huge.log2_tiles, cfg->prune_slabs != 0).total;
+        const uint64_t bytes = e->huge_slab_bytes * cfg->huge.ctas;
+        st = dmalloc(&e->huge_slabs, bytes);
+        if (!st)
+            st = cuda_status(gwfa::launch_slab_init(e->huge_slabs, e->huge_slab_bytes, cfg->huge.ctas,
+                                                    cfg->huge.log2_tiles, cfg->prune_slabs != 0,
+                                                    e->stream));
+        e->device_bytes += bytes;
+    }
+    if (!st) st = cuda_status(cudaStreamCreateWithFlags(&e->side2, cudaStreamNonBlocking));
+    if (!st) st = cuda_status(cudaEventCreateWithFlags(&e->ev_join2, cudaEventDisableTiming));
     if (!st && cfg->wide.ctas) {
         e->wide_slab_bytes = gwfa::slab_layout(cfg->wide.log2_tiles, cfg->prune_slabs != 0).total;
         const uint64_t bytes = e->wide_slab_bytes * cfg->wide.ctas;
@@ -454,27 +470,32 @@ int gwfa_engine_last_retries(gwfa_engine *e, uint32_t *out) {
     return st;
 }
 
-int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, uint32_t *h_order,
-                       uint32_t *n_wide) {
-    if ((n && (!h_pred || !h_order)) || !n_wide) return GWFA_ERR_INVALID;
-    std::vector<uint32_t> big, small;
+int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, uint64_t wide_tiles,
+                       uint32_t *h_order, gwfa_schedule *out) {
+    if ((n && (!h_pred || !h_order)) || !out) return GWFA_ERR_INVALID;
+    std::vector<uint32_t> huge, big, small;
     // diagonals -> hash tiles: on the benchmark graphs a claimed 8-diagonal tile
     // holds about 6 visited diagonals; 0.25 tiles per diagonal leaves a margin of 1.5
     const double tile_per_diag = 0.25;
     for (uint32_t i = 0; i < n; ++i) {
         const double tiles = std::expm1((double)h_pred[(uint64_t)i * 4 + 2]) * tile_per_diag;
-        (tiles > (double)tier0_tiles ? big : small).push_back(i);
+        if (wide_tiles && tiles > (double)wide_tiles) huge.push_back(i);
+        else if (tiles > (double)tier0_tiles) big.push_back(i);
+        else small.push_back(i);
     }
     auto by_cells = [&](uint32_t a, uint32_t b) {
         const float ca = h_pred[(uint64_t)a * 4 + 3], cb = h_pred[(uint64_t)b * 4 + 3];
         return ca != cb ? ca > cb : a < b;
     };
+    std::sort(huge.begin(), huge.end(), by_cells);
     std::sort(big.begin(), big.end(), by_cells);
     std::sort(small.begin(), small.end(), by_cells);
     uint32_t k = 0;
+    for (uint32_t i : huge) h_order[k++] = i;
     for (uint32_t i : big) h_order[k++] = i;
     for (uint32_t i : small) h_order[k++] = i;
-    *n_wide = (uint32_t)big.size();
+    out->n_huge = (uint32_t)huge.size();
+    out->n_wide = (uint32_t)big.size();
     return GWFA_OK;
 }
 
@@ -501,109 +522,134 @@ int gwfa_pack_queries_device(uint32_t n_queries, const char *d_q, const uint64_t
                                          (cudaStream_t)stream));
 }
 
+// Arguments of one alignment launch over queue positions [offset, offset + count)
+// of `list` (or of the retry list given by list_count).
+static TierArgs tier_args(gwfa_engine *e, const uint32_t *d_words, const uint64_t *d_q_off,
+                          const uint32_t *d_vs, const uint32_t *d_ve, const int32_t *d_status,
+                          const gwfa_opts &o, gwfa_result *d_out) {
+    TierArgs a{};
+    a.g = e->g->dev();
+    a.qwords = d_words;
+    a.q_off = d_q_off;
+    a.v_s = d_vs;
+    a.v_e = d_ve;
+    a.qstatus = d_status;
+    a.out = d_out;
+    a.max_lag = o.max_lag;
+    a.max_score = o.max_score;
+    a.stats = e->stats;
+    a.traceback = o.traceback ? 1 : 0;
+    a.paths = e->paths;
+    a.path_len = e->path_len;
+    a.path_cap = e->path_cap;
+    return a;
+}
+
 static int run_tiers(gwfa_engine *e, uint32_t n, const uint32_t *d_words, const uint64_t *d_q_off,
                      const uint32_t *d_vs, const uint32_t *d_ve, const uint32_t *d_order,
-                     uint32_t n_wide, const int32_t *d_status, const gwfa_opts &o,
+                     const gwfa_schedule *sched, const int32_t *d_status, const gwfa_opts &o,
                      gwfa_result *d_out, cudaStream_t s) {
     int st = engine_retry_capacity(e, n);
     if (st) return st;
     const uint32_t T = e->cfg.n_tiers;
     uint32_t *heads = e->counters, *rcount = e->counters + GWFA_MAX_TIERS;
-    uint32_t *wide_head = e->counters + 2 * GWFA_MAX_TIERS;
     st = cuda_status(cudaMemsetAsync(e->counters, 0, 256, s));
     if (st) return st;
     const bool prune = o.max_lag > 0 || o.traceback;   // 64-bit values
     e->last_launches = 0;
-    if (!e->wide_slabs) n_wide = 0;
-    n_wide = std::min(n_wide, n);
-    // wide and tier-0 CTAs must be resident together (tier 0 would otherwise fill
-    // every SM slot first and the heaviest queries would start only after it):
-    // tier 0 gives up the room of the wide CTAs it runs beside
+    // queue order: [huge | wide | tier 0]; the two first classes run on their own
+    // CTAs, concurrently with tier 0, and hand their overflows to the retry tiers
+    uint32_t n_huge = sched && e->huge_slabs ? std::min(sched->n_huge, n) : 0;
+    uint32_t n_wide = sched && e->wide_slabs ? std::min(sched->n_wide, n - n_huge) : 0;
+    struct Cls {
+        const gwfa_tier *tier;
+        uint8_t *slabs;
+        uint64_t slab_bytes;
+        cudaStream_t side;
+        cudaEvent_t join;
+        uint32_t count, offset, *head, *retry, *retry_count;
+    } cls[2] = {
+        {&e->cfg.huge, e->huge_slabs, e->huge_slab_bytes, e->side2, e->ev_join2, n_huge, 0,
+         e->counters + 2 * GWFA_MAX_TIERS + 1, T > 1 ? e->retry_lists + (uint64_t)(T - 2) * e->retry_cap : nullptr,
+         rcount + (T > 1 ? T - 2 : 0)},
+        {&e->cfg.wide, e->wide_slabs, e->wide_slab_bytes, e->side, e->ev_join, n_wide, n_huge,
+         e->counters + 2 * GWFA_MAX_TIERS, T > 1 ? e->retry_lists : nullptr, rcount},
+    };
+    // the classes' CTAs and tier 0's must be resident together (tier 0 would
+    // otherwise fill every SM slot and the heaviest queries would start only after
+    // it): tier 0 gives up the room of the class CTAs it runs beside
     const uint32_t t0_threads = e->cfg.tiers[0].threads ? e->cfg.tiers[0].threads : e->cfg.threads;
-    const uint32_t w_threads = e->cfg.wide.threads ? e->cfg.wide.threads : e->cfg.threads;
-    const uint32_t wctas = n_wide ? std::min(e->cfg.wide.ctas, n_wide) : 0;
-    const uint32_t t0_yield = (uint32_t)(((uint64_t)wctas * w_threads + t0_threads - 1) / t0_threads);
+    uint64_t yield_threads = 0;
+    uint32_t cctas[2] = {0, 0};
+    for (int c = 0; c < 2; ++c) {
+        if (!cls[c].count) continue;
+        const uint32_t th = cls[c].tier->threads ? cls[c].tier->threads : e->cfg.threads;
+        cctas[c] = std::min(cls[c].tier->ctas, cls[c].count);
+        yield_threads += (uint64_t)cctas[c] * th;
+    }
+    const uint32_t t0_yield = (uint32_t)((yield_threads + t0_threads - 1) / t0_threads);
     const uint32_t t0_ctas = e->cfg.tiers[0].ctas > t0_yield ? e->cfg.tiers[0].ctas - t0_yield : 1;
-    if (n_wide > 0) {
-        // the heaviest queries on wide CTAs, concurrently with tier 0 on the rest;
-        // their capacity failures join tier 0's retry list
-        TierArgs a{};
-        a.g = e->g->dev();
-        a.qwords = d_words;
-        a.q_off = d_q_off;
-        a.v_s = d_vs;
-        a.v_e = d_ve;
-        a.qstatus = d_status;
-        a.out = d_out;
+    bool forked = false;
+    for (int c = 0; c < 2; ++c) {
+        if (!cls[c].count) continue;
+        if (!forked) {
+            st = cuda_status(cudaEventRecord(e->ev_fork, s));
+            if (st) return st;
+            forked = true;
+        }
+        TierArgs a = tier_args(e, d_words, d_q_off, d_vs, d_ve, d_status, o, d_out);
         a.list = d_order;
-        a.list_count = nullptr;
-        a.count_val = n_wide;
-        a.list_offset = 0;
-        a.retry = T > 1 ? e->retry_lists : nullptr;
-        a.retry_count = rcount;
-        a.head = wide_head;
-        a.slabs = e->wide_slabs;
-        a.slab_bytes = e->wide_slab_bytes;
-        a.log2cap = e->cfg.wide.log2_tiles;
-        a.max_lag = o.max_lag;
-        a.max_score = o.max_score;
-        a.stats = e->stats;
-        a.traceback = o.traceback ? 1 : 0;
-        a.paths = e->paths;
-        a.path_len = e->path_len;
-        a.path_cap = e->path_cap;
-        st = cuda_status(cudaEventRecord(e->ev_fork, s));
-        if (!st) st = cuda_status(cudaStreamWaitEvent(e->side, e->ev_fork, 0));
-        if (!st) st = cuda_status(gwfa::launch_align(a, prune, wctas, w_threads, e->side));
-        if (!st) st = cuda_status(cudaEventRecord(e->ev_join, e->side));
+        a.count_val = cls[c].count;
+        a.list_offset = cls[c].offset;
+        a.retry = cls[c].retry;
+        a.retry_count = cls[c].retry_count;
+        a.head = cls[c].head;
+        a.slabs = cls[c].slabs;
+        a.slab_bytes = cls[c].slab_bytes;
+        a.log2cap = cls[c].tier->log2_tiles;
+        const uint32_t th = cls[c].tier->threads ? cls[c].tier->threads : e->cfg.threads;
+        st = cuda_status(cudaStreamWaitEvent(cls[c].side, e->ev_fork, 0));
+        if (!st) st = cuda_status(gwfa::launch_align(a, prune, cctas[c], th, cls[c].side));
+        if (!st) st = cuda_status(cudaEventRecord(cls[c].join, cls[c].side));
         if (st) return st;
         e->last_launches++;
     }
+    auto join_classes = [&]() -> int {
+        for (int c = 0; c < 2; ++c)
+            if (cls[c].count) {
+                const int r = cuda_status(cudaStreamWaitEvent(s, cls[c].join, 0));
+                if (r) return r;
+            }
+        return GWFA_OK;
+    };
     for (uint32_t t = 0; t < T; ++t) {
-        if (t == 1 && n_wide > 0) {
-            st = cuda_status(cudaStreamWaitEvent(s, e->ev_join, 0));
+        if (t == 1) {
+            st = join_classes();   // the retry tiers also take the classes' overflows
             if (st) return st;
         }
-        TierArgs a{};
-        a.g = e->g->dev();
-        a.qwords = d_words;
-        a.q_off = d_q_off;
-        a.v_s = d_vs;
-        a.v_e = d_ve;
-        a.qstatus = d_status;
-        a.out = d_out;
+        TierArgs a = tier_args(e, d_words, d_q_off, d_vs, d_ve, d_status, o, d_out);
         a.list = t == 0 ? d_order : e->retry_lists + (uint64_t)(t - 1) * e->retry_cap;
         a.list_count = t == 0 ? nullptr : rcount + (t - 1);
-        a.count_val = t == 0 ? n - n_wide : n;
-        a.list_offset = t == 0 ? n_wide : 0;
+        a.count_val = t == 0 ? n - n_huge - n_wide : n;
+        a.list_offset = t == 0 ? n_huge + n_wide : 0;
         a.retry = t + 1 < T ? e->retry_lists + (uint64_t)t * e->retry_cap : nullptr;
         a.retry_count = rcount + t;
         a.head = heads + t;
         a.slabs = e->slabs[t];
         a.slab_bytes = e->slab_bytes[t];
         a.log2cap = e->cfg.tiers[t].log2_tiles;
-        a.max_lag = o.max_lag;
-        a.max_score = o.max_score;
-        a.stats = e->stats;
-        a.traceback = o.traceback ? 1 : 0;
-        a.paths = e->paths;
-        a.path_len = e->path_len;
-        a.path_cap = e->path_cap;
         const uint32_t th = e->cfg.tiers[t].threads ? e->cfg.tiers[t].threads : e->cfg.threads;
         st = cuda_status(gwfa::launch_align(a, prune, t == 0 ? t0_ctas : e->cfg.tiers[t].ctas, th, s));
         if (st) return st;
         e->last_launches++;
     }
-    if (T == 1 && n_wide > 0) {
-        st = cuda_status(cudaStreamWaitEvent(s, e->ev_join, 0));
-        if (st) return st;
-    }
+    if (T == 1) return join_classes();
     return GWFA_OK;
 }
 
 int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
                             const uint64_t *d_q_off, const uint32_t *d_vs, const uint32_t *d_ve,
-                            const uint32_t *d_order, uint32_t n_wide, const int32_t *d_status,
+                            const uint32_t *d_order, const gwfa_schedule *sched, const int32_t *d_status,
                             const gwfa_opts *opts, gwfa_result *d_out, void *stream) {
     if (!e || !d_words || !d_q_off || !d_vs || !d_ve || !d_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
@@ -615,13 +661,13 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
     if (st) return st;
     // exactly the caller's stream (NULL = the legacy default stream), so the batch is
     // ordered after whatever produced its inputs on that stream
-    return run_tiers(e, n, d_words, d_q_off, d_vs, d_ve, d_order, n_wide, d_status, o, d_out,
+    return run_tiers(e, n, d_words, d_q_off, d_vs, d_ve, d_order, sched, d_status, o, d_out,
                      (cudaStream_t)stream);
 }
 
 int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t *h_q_off,
                      const uint32_t *h_vs, const uint32_t *h_ve, const uint32_t *h_order,
-                     uint32_t n_wide, const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
+                     const gwfa_schedule *sched, const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
     if (!e || !h_q_off || !h_vs || !h_ve || !h_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
     if (o.max_lag < 0 || (o.traceback && o.max_lag != 0)) return GWFA_ERR_INVALID;
@@ -656,7 +702,7 @@ int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t
     if (!st && h_order) st = cuda_status(cudaMemcpyAsync(d_order, h_order, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
     if (!st) st = cuda_status(gwfa::launch_pack(n, d_q, d_off, d_words, d_status, s));
     if (!st)
-        st = run_tiers(e, n, d_words, d_off, d_vs, d_ve, h_order ? d_order : nullptr, n_wide, d_status, o,
+        st = run_tiers(e, n, d_words, d_off, d_vs, d_ve, h_order ? d_order : nullptr, sched, d_status, o,
                        d_out, s);
     if (!st) e->last_launches += 1;
     if (!st) st = cuda_status(cudaMemcpyAsync(h_out, d_out, (uint64_t)n * sizeof(gwfa_result), cudaMemcpyDeviceToHost, s));

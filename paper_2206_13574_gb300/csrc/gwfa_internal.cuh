@@ -187,10 +187,10 @@ struct gwfa_engine {
     gwfa_engine_config cfg{};
     uint8_t *slabs[GWFA_MAX_TIERS] = {};
     uint64_t slab_bytes[GWFA_MAX_TIERS] = {};
-    uint8_t *wide_slabs = nullptr;
-    uint64_t wide_slab_bytes = 0;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    uint8_t *wide_slabs = nullptr, *huge_slabs = nullptr;
+    uint64_t wide_slab_bytes = 0, huge_slab_bytes = 0;
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     uint32_t *counters = nullptr;   // per tier: head, retry_count; plus retry lists
     uint32_t *retry_lists = nullptr;
     uint64_t retry_cap = 0;

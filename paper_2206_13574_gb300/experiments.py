@@ -111,36 +111,53 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300) -> d
     pred = m4.predict(m4.features(b0)).cpu().numpy()
     base = gw.default_config(gr4)
     total = base.tiers[0].ctas
-    l_order, l_wide = gw.plan_schedule(pred, int(0.75 * (1 << base.tiers[0].log2_tiles)))
-    w_ctas = costmodel.wide_ctas(pred, l_order, l_wide, total, coeffs)
+    wide_log2, huge_log2 = 20, 23
 
-    def engine(wide: int):
+    def engine(wide: int = 0, huge: int = 0):
         cfg = gw.default_config(gr4)
         cfg.tiers[1].ctas, cfg.tiers[1].log2_tiles = 152, 20
         cfg.tiers[2].ctas, cfg.tiers[2].log2_tiles = 19, 23
-        cfg.wide.ctas, cfg.wide.log2_tiles, cfg.wide.threads = wide, 20, 512
+        cfg.wide.ctas, cfg.wide.log2_tiles, cfg.wide.threads = wide, wide_log2, 512
+        cfg.huge.ctas, cfg.huge.log2_tiles, cfg.huge.threads = huge, huge_log2, 512
         return gw.Engine(gr4, config=cfg)
 
+    probe = engine(1, 1).config
+    l_order, l_huge, l_wide = gw.plan_schedule(pred, *costmodel.capacities(probe))
+    # one CTA per huge query (they are few and each is a long tail on its own);
+    # wide CTAs by the wide class's share of the predicted time
+    h_ctas = min(l_huge, 32)
+    w_ctas = costmodel.wide_ctas(pred, l_order, l_wide, total, coeffs, first=l_huge)
     out = {"workload": f"config4: 50 Mb graph, {n} lognormal 1-100 kb queries, 0.1-10% divergence, exact",
            "train": f"{len(q2)} config-2 + {len(q3)} config-3-graph queries, 2000 Adam steps",
-           "learned_wide_ctas": w_ctas, "time_coeffs_us": list(coeffs)}
+           "learned_huge": [int(l_huge), int(h_ctas), huge_log2], "learned_wide": [int(l_wide), int(w_ctas), wide_log2],
+           "time_coeffs_us": list(coeffs)}
     ref = None
-    plans = {"plain_fifo": (None, 0, 0), "plain_longest_first": (np.argsort(-q4.lengths(), kind="stable"), 0, 0),
-             "learned": (l_order, l_wide, w_ctas)}
-    for name, (order, nw, wc) in plans.items():
-        eng = engine(wc)
+    plans = {"plain_fifo": (None, 0, 0, 0, 0),
+             "plain_longest_first": (np.argsort(-q4.lengths(), kind="stable"), 0, 0, 0, 0),
+             "learned_wide_only": (*gw.plan_schedule(pred, int(0.75 * (1 << base.tiers[0].log2_tiles)))[::2],
+                                   0, 0, 0),
+             "learned": (l_order, l_huge, l_wide, h_ctas, w_ctas)}
+    o2, nw2 = plans["learned_wide_only"][:2]
+    plans["learned_wide_only"] = (o2, 0, nw2, 0, costmodel.wide_ctas(pred, o2, nw2, total, coeffs))
+    for name, (order, nh, nw, hc, wc) in plans.items():
+        eng = engine(wc, hc)
         b = gw.DeviceBatch(q4, order=None if order is None else np.asarray(order, np.uint32))
-        b.run(eng, n_wide=nw)
-        t = _timed_run(eng, b, n_wide=nw)
+        b.run(eng, n_wide=nw, n_huge=nh)
+        t = _timed_run(eng, b, n_wide=nw, n_huge=nh)
         r = b.results()
         retries = eng.last_retries()
         if ref is None:
             ref = r
         assert np.array_equal(r["edit_distance"], ref["edit_distance"])
         out[name] = {"s": t, "gbp_per_s": float(q4.lengths()[r["status"] == 0].sum()) / t / 1e9,
-                     "tier0_overflows": int(retries[0]), "tier1_overflows": int(retries[1]), "n_wide": int(nw),
+                     "tier0_overflows": int(retries[0]), "tier1_overflows": int(retries[1]),
+                     "n_huge": int(nh), "n_wide": int(nw), "huge_ctas": int(hc), "wide_ctas": int(wc),
                      "ok": int((r["status"] == 0).sum()), "slab_bytes": eng.device_bytes}
         eng.close()
+    # where the time goes: the heaviest queries' own CTA times against the batch
+    top = np.argsort(-ref["device_us"].astype(np.float64))[:8]
+    out["slowest_queries"] = [{"len": int(q4.lengths()[i]), "us": int(ref["device_us"][i]),
+                               "cells": int(ref["cells"][i]), "visited": int(ref["visited"][i])} for i in top]
     out["cells"] = int(ref["cells"].sum())
     out["spearman_pred_cells"] = costmodel.spearman(pred[:, 3], np.log1p(ref["cells"].astype(np.float64)))
     out["r2_log_cells"] = float(costmodel.r2(pred[:, 3:4], np.log1p(ref["cells"].astype(np.float64))[:, None])[0])

@@ -31,7 +31,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gw.gwfa_result) == 56
     assert gw.RESULT_DTYPE.itemsize == 56
     assert ctypes.sizeof(gw.gwfa_opts) == 16
-    assert ctypes.sizeof(gw.gwfa_engine_config) == 112   # 92 bytes of u32 fields, padded to 8
+    assert ctypes.sizeof(gw.gwfa_engine_config) == 128   # 108 bytes of u32 fields, padded to 8
+    assert ctypes.sizeof(gw.gwfa_schedule) == 8
     for name, _ in gw.gwfa_result._fields_:
         assert name in gw.RESULT_DTYPE.names
 

@@ -70,12 +70,18 @@ def test_plan_schedule_orders_by_predicted_work_and_routes_big():
     pred = np.zeros((6, 4), dtype=np.float32)
     pred[:, 3] = [3, 9, 1, 7, 5, 2]                 # log1p cells
     pred[:, 2] = [1, 1, 1, 20, 1, 21]                # log1p visited: queries 3 and 5 are huge
-    order, n_wide = gw.plan_schedule(pred, tier0_tiles=1000)
-    assert n_wide == 2
+    order, n_huge, n_wide = gw.plan_schedule(pred, tier0_tiles=1000)
+    assert (n_huge, n_wide) == (0, 2)
     assert list(order[:2]) == [3, 5]                 # big ones first, by predicted cells
     assert list(order[2:]) == [1, 4, 0, 2]           # the rest longest-predicted-first
-    order, n_wide = gw.plan_schedule(pred, tier0_tiles=10 ** 12)
-    assert n_wide == 0 and list(order) == [1, 3, 4, 0, 5, 2]
+    order, n_huge, n_wide = gw.plan_schedule(pred, tier0_tiles=10 ** 12)
+    assert n_huge == 0 and n_wide == 0 and list(order) == [1, 3, 4, 0, 5, 2]
+    # predicted tiles = expm1(visited) / 4: query 3 ~1.2e8, query 5 ~3.3e8; a 2e8 wide
+    # class takes query 3 and leaves query 5 to the huge class, a 1e8 one takes neither
+    order, n_huge, n_wide = gw.plan_schedule(pred, tier0_tiles=1000, wide_tiles=2 * 10 ** 8)
+    assert (n_huge, n_wide) == (1, 1) and list(order[:2]) == [5, 3]
+    order, n_huge, n_wide = gw.plan_schedule(pred, tier0_tiles=1000, wide_tiles=10 ** 8)
+    assert (n_huge, n_wide) == (2, 0) and list(order[:2]) == [3, 5]
 
 
 # ------------------------------------------------------------------ GPU
@@ -158,7 +164,8 @@ def test_learned_schedule_keeps_results_and_avoids_overflow_reruns(c2small):
     b.run(eng)
     plain = b.results()
     plain_retries = int(eng.last_retries()[0])
-    order, n_wide = costmodel.plan(m, b, eng)
+    order, n_huge, n_wide = costmodel.plan(m, b, eng)
+    assert n_huge == 0                       # no huge class in this engine
     b2 = gw.DeviceBatch(test, order=order)
     b2.run(eng, n_wide=n_wide)
     learned = b2.results()

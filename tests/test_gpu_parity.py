@@ -143,6 +143,37 @@ def test_batch_order_and_tiers_do_not_change_results():
             assert np.array_equal(base[f], res2[f]), f
 
 
+@pytest.mark.parametrize("tiers", [3, 2, 1])
+def test_concurrent_classes_do_not_change_results(tiers):
+    """Huge and wide classes beside tier 0, all with small slabs so overflows cross
+    from each class to the retry tiers; every counter equals the default engine's."""
+    g, qs = synth.make_config(2, n_queries=300)
+    graph = gw.Graph.from_synth(g)
+    base = gw.Engine(graph).align_batch(qs.seq, qs.off, qs.v_s, qs.v_e)
+    perm = np.random.default_rng(1).permutation(len(qs)).astype(np.uint32)
+    cfg = gw.default_config(graph)
+    cfg.n_tiers = tiers
+    cfg.tiers[0].ctas, cfg.tiers[0].log2_tiles = 96, 10
+    if tiers > 1:
+        cfg.tiers[1].ctas, cfg.tiers[1].log2_tiles = 16, 13 if tiers > 2 else 18
+    cfg.wide.ctas, cfg.wide.log2_tiles = 24, 11
+    cfg.huge.ctas, cfg.huge.log2_tiles = 5, 12
+    eng = gw.Engine(graph, config=cfg)
+    res = eng.align_batch(qs.seq, qs.off, qs.v_s, qs.v_e, order=perm, n_huge=40, n_wide=60)
+    assert eng.last_launches == tiers + 2 + 1   # tiers, both classes, the query packing
+    if tiers == 1:   # no retry tier: overflows end as CAPACITY, the rest must match
+        ok = res["status"] == 0
+        assert np.all((res["status"] == 0) | (res["status"] == gw.GWFA_ERR_CAPACITY))
+        assert ok.sum() > 100
+    else:
+        ok = np.ones(len(qs), dtype=bool)
+        assert np.all(res["status"] == 0)
+        assert eng.last_retries()[0] > 0
+    for f in gw.RESULT_DTYPE.names:
+        if f != "device_us":
+            assert np.array_equal(base[f][ok], res[f][ok]), f
+
+
 def test_capacity_error_without_retry_tier():
     g, qs = synth.make_config(2, n_queries=50)
     graph = gw.Graph.from_synth(g)
