@@ -216,8 +216,22 @@ def ncu_case(args):
         b.run(eng)
     torch.cuda.synchronize()
     r = b.results()
-    print(json.dumps({"ncu_case": True, "engine_bytes": eng.device_bytes, "ok": int((r["status"] == 0).sum()),
-                      "cells": int(r["cells"].sum()), "bases": int(qs.lengths().sum())}))
+    retries = [int(x) for x in eng.last_retries()[:2]]
+    eng.close()
+    # after the captured launches: the same tier 0 alone, so that the work of the
+    # captured tier-0 launch is known (queries that overflow it end as CAPACITY)
+    c.n_tiers = 1
+    e1 = gw.Engine(graph, config=c)
+    b.run(e1)
+    torch.cuda.synchronize()
+    r1 = b.results()
+    ok1 = r1["status"] == 0
+    print(json.dumps({"ncu_case": True, "ok": int((r["status"] == 0).sum()),
+                      "cells": int(r["cells"].sum()), "bases": int(qs.lengths().sum()), "retries": retries,
+                      "tier0_completed": int(ok1.sum()), "tier0_completed_cells": int(r1["cells"][ok1].sum()),
+                      # an overflowing query reports the cells it processed before it overflowed
+                      "tier0_launch_cells": int(r1["cells"].sum()),
+                      "tier0_overflows": int((r1["status"] == gw.GWFA_ERR_CAPACITY).sum())}))
 
 
 def measured_traffic_per_cell():

@@ -281,6 +281,62 @@ int gwfa_engine_set_stats(gwfa_engine *e, uint64_t *d_stats);
  * last stream): out[t] = queries that tier t handed to tier t+1 (t < GWFA_MAX_TIERS - 1) */
 int gwfa_engine_last_retries(gwfa_engine *e, uint32_t *out);
 
+/* ---- base-level alignment along the walk -------------------------------- */
+/*
+ * Gwfa returns a distance and (Alg. 5-6) a vertex walk, not a base-level
+ * alignment; the paper's discussion (Sec. 4) obtains one by aligning the query
+ * to the sequence the walk spells with a pairwise method.  This step does that on
+ * the device: for each query it spells sigma(w) (2-bit packed) and runs a
+ * pairwise edit-distance wavefront alignment (unit costs, both ends global)
+ * bounded by the query's reported distance, then walks the stored wavefronts
+ * back to a CIGAR.  When w is optimal the CIGAR has exactly edit_distance edits.
+ *
+ * CIGAR operations are uint32 (length << 4 | op) with the BAM op codes below,
+ * query = the read, walk = the reference: '=' a run of equal bases, 'X' one
+ * substituted base, 'I' a query base absent from the walk, 'D' a walk base absent
+ * from the query.  Adjacent operations of one kind are merged.
+ */
+#define GWFA_CIGAR_INS 1
+#define GWFA_CIGAR_DEL 2
+#define GWFA_CIGAR_EQ 7
+#define GWFA_CIGAR_DIFF 8
+typedef struct gwfa_cigar gwfa_cigar;
+typedef struct {
+    int32_t status;       /* GWFA_OK; GWFA_ERR_NOT_RUN (the query's alignment did not
+                             succeed); GWFA_ERR_CAPACITY (walk truncated at path_cap,
+                             workspace too small, or more than cigar_cap operations:
+                             n_ops still tells how many); GWFA_ERR_SCORE_LIMIT (the walk
+                             is farther than edit_distance from the query) */
+    int32_t cost;         /* edits of the CIGAR */
+    uint32_t n_ops;       /* CIGAR operations */
+    uint32_t walk_len;    /* bases spelled by the walk */
+} gwfa_cigar_result;      /* 16 bytes */
+
+/*
+ * ctas: persistent CTAs (0 = 2 per SM); workspace_bytes: device scratch per CTA
+ * (0 = 8 MiB).  A query needs 4 * (|sigma(w)| / 16 + 2) + 4 * (d + 1)^2 bytes
+ * (rounded up to 16) of it: the default holds distances up to ~1400 for walks of
+ * tens of kb.  The workspace is allocated here; gwfa_cigar_device allocates
+ * nothing.
+ */
+int gwfa_cigar_create(const gwfa_graph *g, uint32_t ctas, uint64_t workspace_bytes, gwfa_cigar **out);
+int gwfa_cigar_destroy(gwfa_cigar *c);
+/*
+ * Asynchronous on `stream` (NULL = legacy default stream), device pointers:
+ *   d_words, d_q_off  the packed batch (as for gwfa_align_batch_device)
+ *   d_res             the batch's results (status, edit_distance are read)
+ *   d_paths, path_cap, d_path_len   the walks written by a traceback batch
+ *                     (gwfa_engine_set_paths)
+ *   d_cigar           n_queries * cigar_cap operations; query i writes from
+ *                     d_cigar[i * cigar_cap]
+ *   d_out             n_queries results
+ * Calls on one gwfa_cigar share its workspace: order them on one stream.
+ */
+int gwfa_cigar_device(gwfa_cigar *c, uint32_t n_queries, const uint32_t *d_words,
+                      const uint64_t *d_q_off, const gwfa_result *d_res, const uint32_t *d_paths,
+                      uint32_t path_cap, const uint32_t *d_path_len, uint32_t *d_cigar,
+                      uint32_t cigar_cap, gwfa_cigar_result *d_out, void *stream);
+
 /* ---- learned cost model (scheduling only; never changes a result) -------- */
 /*
  * A 6 -> 32 -> 32 -> 4 MLP (ReLU; FP16 weights and activations, FP32

@@ -35,6 +35,11 @@ RESULT_DTYPE = np.dtype([("status", "<i4"), ("edit_distance", "<i4"), ("is_upper
                          ("spills", "<u8")])
 assert RESULT_DTYPE.itemsize == 56
 
+# numpy view of gwfa_cigar_result (16 bytes) and the CIGAR op codes (BAM's)
+CIGAR_RESULT_DTYPE = np.dtype([("status", "<i4"), ("cost", "<i4"), ("n_ops", "<u4"), ("walk_len", "<u4")])
+GWFA_CIGAR_INS, GWFA_CIGAR_DEL, GWFA_CIGAR_EQ, GWFA_CIGAR_DIFF = 1, 2, 7, 8
+CIGAR_CHARS = {GWFA_CIGAR_INS: "I", GWFA_CIGAR_DEL: "D", GWFA_CIGAR_EQ: "=", GWFA_CIGAR_DIFF: "X"}
+
 
 class gwfa_opts(ctypes.Structure):
     _fields_ = [("max_lag", ctypes.c_int32), ("traceback", ctypes.c_int32),
@@ -114,6 +119,9 @@ SIGNATURES.update({
     "gwfa_model_train_device": ([_P, _u32, _P, _P, _u32, _u32, ctypes.c_float, _u64, _P, _P],
                                 ctypes.c_int),
     "gwfa_plan_schedule": ([_u32, _P, _u64, _u64, _P, _P], ctypes.c_int),
+    "gwfa_cigar_create": ([_P, _u32, _u64, ctypes.POINTER(_P)], ctypes.c_int),
+    "gwfa_cigar_destroy": ([_P], ctypes.c_int),
+    "gwfa_cigar_device": ([_P, _u32, _P, _P, _P, _P, _u32, _P, _P, _u32, _P, _P], ctypes.c_int),
 })
 
 
@@ -470,6 +478,54 @@ def plan_schedule(pred: np.ndarray, tier0_tiles: int, wide_tiles: int = 0):
     _check(load().gwfa_plan_schedule(n, pred.ctypes.data, int(tier0_tiles), int(wide_tiles),
                                      order.ctypes.data, ctypes.byref(sc)), "gwfa_plan_schedule")
     return order, int(sc.n_huge), int(sc.n_wide)
+
+
+class Cigar:
+    """Base-level alignment of queries to their walks (gwfa_cigar_*): a workspace of
+    `ctas` x `workspace_bytes` on the graph's GPU (0 = library defaults)."""
+
+    def __init__(self, graph: Graph, ctas: int = 0, workspace_bytes: int = 0):
+        h = _P()
+        _check(load().gwfa_cigar_create(graph.handle, int(ctas), int(workspace_bytes), ctypes.byref(h)),
+               "gwfa_cigar_create")
+        self.graph = graph
+        self.handle = h
+
+    def run_device(self, n: int, d_words: int, d_q_off: int, d_res: int, d_paths: int, path_cap: int,
+                   d_path_len: int, d_cigar: int | None, cigar_cap: int, d_out: int, stream: int = 0):
+        _check(load().gwfa_cigar_device(self.handle, n, d_words, d_q_off, d_res, d_paths, path_cap,
+                                        d_path_len, d_cigar or None, cigar_cap, d_out, stream or None),
+               "gwfa_cigar_device")
+
+    def run(self, batch: "DeviceBatch", paths, path_len, path_cap: int, cigar_cap: int = 1024,
+            stream=None):
+        """CIGARs of a batch after a traceback run whose walks are in the device
+        tensors `paths` / `path_len`; returns (ops tensor n x cigar_cap, results tensor)."""
+        import torch
+        dev = batch.q.device
+        ops = torch.zeros(batch.n * cigar_cap, dtype=torch.int32, device=dev)
+        out = torch.empty(batch.n * CIGAR_RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.run_device(batch.n, batch.words.data_ptr(), batch.q_off.data_ptr(), batch.out.data_ptr(),
+                        paths.data_ptr(), path_cap, path_len.data_ptr(), ops.data_ptr(), cigar_cap,
+                        out.data_ptr(), st.cuda_stream)
+        return ops, out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gwfa_cigar_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cigar_string(ops) -> str:
+    """Text form of CIGAR operations (uint32 length << 4 | op)."""
+    return "".join(f"{int(o) >> 4}{CIGAR_CHARS[int(o) & 15]}" for o in np.asarray(ops, dtype=np.uint32))
 
 
 class Server:

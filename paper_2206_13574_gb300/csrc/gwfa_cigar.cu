@@ -1,0 +1,362 @@
+// gwfa_cigar.cu -- base-level alignment of each query to the sequence its walk spells.
+//
+// Gwfa (Alg. 1-6) yields the edit distance and one optimal vertex walk w.  The
+// paper's discussion (Sec. 4) gets the base-level alignment by aligning the query
+// to sigma(w) with a pairwise method; here that is an edit-distance wavefront
+// alignment on the device, one persistent CTA per query at a time:
+//
+//   1. spell sigma(w) into the CTA's workspace, 2-bit packed like the graph labels
+//      (a block-wide prefix sum of the label lengths gives each vertex's position);
+//   2. for s = 0, 1, ... compute the furthest point of every diagonal k = j - i
+//      (i in the query, j in the walk) at score s from score s - 1 (substitution
+//      i+1, j+1; query base skipped i+1; walk base skipped j+1), extend it along
+//      equal bases 16 at a time (XOR of packed windows, first set bit), and keep
+//      every wavefront: score s occupies s^2 .. s^2 + 2s of the array;
+//   3. once the end point (n, m) is on a wavefront, one thread walks the stored
+//      wavefronts back: each step re-derives which predecessor gave the point's
+//      starting offset, emitting the run of equal bases and one edit.
+//
+// The score loop is bounded by the query's Gwfa distance d: when w is optimal,
+// the pairwise distance of q and sigma(w) is d (an alignment of q to a walk is
+// an alignment to its spelled sequence and back), so (d+1)^2 offsets suffice.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "gwfa_internal.cuh"
+
+struct gwfa_cigar {
+    const gwfa_graph *g = nullptr;
+    uint32_t ctas = 0;
+    uint64_t ws_bytes = 0;    // per CTA
+    uint8_t *ws = nullptr;    // ctas * ws_bytes
+    uint32_t *head = nullptr; // work-queue counter
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct CigarArgs {
+    gwfa::DevGraph g;
+    const uint32_t *qwords;
+    const uint64_t *q_off;
+    const gwfa_result *res;
+    const uint32_t *paths;
+    uint32_t path_cap;
+    const uint32_t *path_len;
+    uint32_t *cigar;
+    uint32_t cigar_cap;
+    gwfa_cigar_result *out;
+    uint8_t *ws;
+    uint64_t ws_bytes;
+    uint32_t n;
+    uint32_t *head;
+};
+
+// 16 bases from base position p of a packed stream (base t of a word in bits
+// 2t..2t+1); the query words are read-only here, the walk words are written by
+// this CTA, so they are read from L2.
+__device__ __forceinline__ uint32_t q16(const uint32_t *w, uint64_t p) {
+    const uint64_t i = p >> 4;
+    return __funnelshift_r(__ldg(w + i), __ldg(w + i + 1), (uint32_t)(p & 15) * 2);
+}
+__device__ __forceinline__ uint32_t t16(const uint32_t *w, uint64_t p) {
+    const uint64_t i = p >> 4;
+    return __funnelshift_r(__ldcg(w + i), __ldcg(w + i + 1), (uint32_t)(p & 15) * 2);
+}
+
+// length of the run of equal bases q[i..] / t[j..], at most maxl
+__device__ int run_length(const uint32_t *qw, int i, const uint32_t *tw, int j, int maxl) {
+    int l = 0;
+    while (l < maxl) {
+        const uint32_t x = q16(qw, (uint64_t)(i + l)) ^ t16(tw, (uint64_t)(j + l));
+        if (x) {
+            l += (__ffs(x) - 1) >> 1;
+            break;
+        }
+        l += 16;
+    }
+    return min(l, maxl);
+}
+
+// The three predecessors of diagonal k at score s (prev = wavefront s - 1, indexed
+// by diagonal): the query offset each would start k at, or -1 where the move is
+// impossible (unreached predecessor, or it would leave the n x m rectangle).
+struct Pred {
+    int sub, ins, del;
+};
+__device__ __forceinline__ Pred predecessors(const int *prev, int s, int k, int n, int m) {
+    Pred p{-1, -1, -1};
+    const int r = s - 1;   // wavefront s - 1 spans diagonals -r .. r
+    if (k >= -r && k <= r) {
+        const int v = __ldcg(prev + k);
+        if (v >= 0 && v < n && v + k < m) p.sub = v + 1;        // (v, v+k) -> (v+1, v+k+1)
+    }
+    if (k + 1 <= r) {
+        const int v = __ldcg(prev + k + 1);
+        if (v >= 0 && v < n) p.ins = v + 1;                     // (v, v+k+1) -> (v+1, v+k+1)
+    }
+    if (k - 1 >= -r) {
+        const int v = __ldcg(prev + k - 1);
+        if (v >= 0 && v + k - 1 < m) p.del = v;                 // (v, v+k-1) -> (v, v+k)
+    }
+    return p;
+}
+
+struct Runs {
+    uint32_t *ops;
+    uint32_t cap, n, op, len;
+    __device__ void emit(uint32_t o, uint32_t l) {
+        if (!l) return;
+        if (len && o == op) {
+            len += l;
+            return;
+        }
+        flush();
+        op = o;
+        len = l;
+    }
+    __device__ void flush() {
+        if (len) {
+            if (n < cap) ops[n] = (len << 4) | op;
+            ++n;
+        }
+        len = 0;
+    }
+};
+
+__device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsigned long long &s_sum,
+                           uint32_t *s_warp, uint32_t &s_base) {
+    const int tid = threadIdx.x;
+    const gwfa_result r = A.res[qid];
+    const uint32_t plen = A.path_len[qid];
+    gwfa_cigar_result o = {GWFA_OK, 0, 0, 0};
+    if (r.status != GWFA_OK || plen == 0) o.status = GWFA_ERR_NOT_RUN;
+    else if (plen > A.path_cap) o.status = GWFA_ERR_CAPACITY;
+    if (o.status) {   // uniform: every thread read the same words
+        if (tid == 0) A.out[qid] = o;
+        return;
+    }
+    const uint32_t *walk = A.paths + (uint64_t)qid * A.path_cap;
+
+    // |sigma(w)|
+    if (tid == 0) s_sum = 0;
+    __syncthreads();
+    unsigned long long part = 0;
+    for (uint32_t i = tid; i < plen; i += blockDim.x) {
+        const uint32_t v = __ldg(walk + i);
+        part += v < A.g.nv ? __ldg(&A.g.vinfo[v]).y : (1ull << 40);   // a bad id fails the size test
+    }
+    atomicAdd(&s_sum, part);
+    __syncthreads();
+    const unsigned long long m64 = s_sum;
+    const int n = (int)(A.q_off[qid + 1] - A.q_off[qid]);
+    const int d = r.edit_distance;
+    const uint64_t t_words = (m64 >> 4) + 2;
+    const uint64_t wf_off = (t_words * 4 + 15) & ~15ull;
+    const uint64_t need = wf_off + (uint64_t)(d + 1) * (uint64_t)(d + 1) * 4;
+    o.walk_len = (uint32_t)min(m64, 0xFFFFFFFFull);
+    if (m64 > 0x3FFFFFFFull || d < 0 || need > A.ws_bytes) {
+        if (tid == 0) {
+            o.status = GWFA_ERR_CAPACITY;
+            A.out[qid] = o;
+        }
+        return;
+    }
+    const int m = (int)m64;
+
+    // 1. spell sigma(w): zero the words, then OR every label in at its position
+    for (uint64_t w = tid; w < t_words; w += blockDim.x) __stcg(tw + w, 0u);
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    for (uint32_t c0 = 0; c0 < plen; c0 += blockDim.x) {
+        const uint32_t i = c0 + tid;
+        uint4 vi = make_uint4(0u, 0u, 0u, 0u);
+        if (i < plen) vi = __ldg(&A.g.vinfo[__ldg(walk + i)]);
+        uint32_t x = vi.y;   // inclusive scan of the lengths in the warp
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t before = s_base;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        const uint32_t pos = before + x - vi.y;
+        const uint32_t *src = A.g.words + vi.x;
+        for (uint32_t b = 0; b < vi.y; b += 16) {
+            uint32_t w = __ldg(src + (b >> 4));
+            const uint32_t nb = min(16u, vi.y - b);
+            if (nb < 16) w &= (1u << (2 * nb)) - 1u;
+            const uint32_t p = pos + b, sh = (p & 15) * 2;
+            atomicOr(tw + (p >> 4), w << sh);
+            if (sh) atomicOr(tw + (p >> 4) + 1, w >> (32 - sh));
+        }
+        __syncthreads();
+        if (tid == (int)blockDim.x - 1) s_base = pos + vi.y;
+        __syncthreads();
+    }
+
+    // 2. wavefronts, score by score, until the end point (n, m) is reached
+    int *wf = (int *)((uint8_t *)tw + wf_off);
+    const uint32_t *qw = A.qwords + (A.q_off[qid] >> 4) + qid;
+    const int k_end = m - n;
+    int found = -1;
+    for (int s = 0; s <= d; ++s) {
+        int *cur = wf + (int64_t)s * s + s;
+        const int *prev = wf + (int64_t)(s - 1) * (s - 1) + (s - 1);
+        bool hit = false;
+        for (int k = -s + tid; k <= s; k += blockDim.x) {
+            int c = -1;
+            if (s == 0) {
+                c = 0;
+            } else {
+                const Pred p = predecessors(prev, s, k, n, m);
+                c = max(p.sub, max(p.ins, p.del));
+            }
+            int i = -1;
+            if (c >= 0 && c <= n && c + k >= 0 && c + k <= m)
+                i = c + run_length(qw, c, tw, c + k, min(n - c, m - c - k));
+            __stcg(cur + k, i);
+            if (k == k_end && i == n) hit = true;
+        }
+        if (__syncthreads_or(hit)) {
+            found = s;
+            break;
+        }
+    }
+
+    // 3. walk back from (n, m) to (0, 0)
+    if (tid == 0) {
+        if (found < 0) {
+            o.status = GWFA_ERR_SCORE_LIMIT;
+            A.out[qid] = o;
+            return;
+        }
+        Runs R{A.cigar + (uint64_t)qid * A.cigar_cap, A.cigar_cap, 0u, 0u, 0u};
+        int s = found, k = k_end, i = n;
+        while (s > 0) {
+            const int *prev = wf + (int64_t)(s - 1) * (s - 1) + (s - 1);
+            const Pred p = predecessors(prev, s, k, n, m);
+            const int c = max(p.sub, max(p.ins, p.del));
+            R.emit(GWFA_CIGAR_EQ, (uint32_t)(i - c));
+            if (p.sub == c) {
+                R.emit(GWFA_CIGAR_DIFF, 1u);
+                i = c - 1;
+            } else if (p.ins == c) {
+                R.emit(GWFA_CIGAR_INS, 1u);
+                i = c - 1;
+                k = k + 1;
+            } else {
+                R.emit(GWFA_CIGAR_DEL, 1u);
+                i = c;
+                k = k - 1;
+            }
+            --s;
+        }
+        R.emit(GWFA_CIGAR_EQ, (uint32_t)i);   // score 0: equal bases from (0, 0)
+        R.flush();
+        if (R.n <= R.cap)   // emitted end to start: reverse in place
+            for (uint32_t a = 0, b = R.n; a + 1 < b; ++a, --b) {
+                const uint32_t t = R.ops[a];
+                R.ops[a] = R.ops[b - 1];
+                R.ops[b - 1] = t;
+            }
+        o.cost = found;
+        o.n_ops = R.n;
+        o.status = R.n <= R.cap ? GWFA_OK : GWFA_ERR_CAPACITY;
+        A.out[qid] = o;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) cigar_kernel(CigarArgs A) {
+    __shared__ uint32_t s_qid, s_base;
+    __shared__ unsigned long long s_sum;
+    __shared__ uint32_t s_warp[kThreads / 32];
+    uint32_t *const tw = (uint32_t *)(A.ws + (uint64_t)blockIdx.x * A.ws_bytes);
+    for (;;) {
+        if (threadIdx.x == 0) s_qid = atomicAdd(A.head, 1u);
+        __syncthreads();
+        const uint32_t qid = s_qid;
+        __syncthreads();
+        if (qid >= A.n) return;
+        align_walk(A, qid, tw, s_sum, s_warp, s_base);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+extern "C" int gwfa_cigar_create(const gwfa_graph *g, uint32_t ctas, uint64_t workspace_bytes,
+                                 gwfa_cigar **out) {
+    if (!g || !out) return GWFA_ERR_INVALID;
+    *out = nullptr;
+    if (cudaSetDevice(g->device) != cudaSuccess) return GWFA_ERR_CUDA;
+    if (ctas == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+            return GWFA_ERR_CUDA;
+        ctas = 2u * (uint32_t)sms;
+    }
+    if (workspace_bytes == 0) workspace_bytes = 8ull << 20;
+    workspace_bytes = (workspace_bytes + 255) & ~255ull;
+    gwfa_cigar *c = new (std::nothrow) gwfa_cigar();
+    if (!c) return GWFA_ERR_OOM;
+    c->g = g;
+    c->ctas = ctas;
+    c->ws_bytes = workspace_bytes;
+    if (cudaMalloc(&c->ws, workspace_bytes * ctas) != cudaSuccess ||
+        cudaMalloc(&c->head, 256) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->ws);
+        cudaFree(c->head);
+        delete c;
+        return GWFA_ERR_OOM;
+    }
+    *out = c;
+    return GWFA_OK;
+}
+
+extern "C" int gwfa_cigar_destroy(gwfa_cigar *c) {
+    if (!c) return GWFA_ERR_INVALID;
+    cudaSetDevice(c->g->device);
+    cudaFree(c->ws);
+    cudaFree(c->head);
+    delete c;
+    return GWFA_OK;
+}
+
+extern "C" int gwfa_cigar_device(gwfa_cigar *c, uint32_t n_queries, const uint32_t *d_words,
+                                 const uint64_t *d_q_off, const gwfa_result *d_res,
+                                 const uint32_t *d_paths, uint32_t path_cap, const uint32_t *d_path_len,
+                                 uint32_t *d_cigar, uint32_t cigar_cap, gwfa_cigar_result *d_out,
+                                 void *stream) {
+    if (!c || !d_words || !d_q_off || !d_res || !d_paths || !d_path_len || !d_out) return GWFA_ERR_INVALID;
+    if (!d_cigar && cigar_cap) return GWFA_ERR_INVALID;
+    if (path_cap == 0) return GWFA_ERR_INVALID;
+    if (n_queries == 0) return GWFA_OK;
+    if (cudaSetDevice(c->g->device) != cudaSuccess) return GWFA_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(c->head, 0, 4, s) != cudaSuccess) return GWFA_ERR_CUDA;
+    CigarArgs a{};
+    a.g = c->g->dev();
+    a.qwords = d_words;
+    a.q_off = d_q_off;
+    a.res = d_res;
+    a.paths = d_paths;
+    a.path_cap = path_cap;
+    a.path_len = d_path_len;
+    a.cigar = d_cigar;
+    a.cigar_cap = cigar_cap;
+    a.out = d_out;
+    a.ws = c->ws;
+    a.ws_bytes = c->ws_bytes;
+    a.n = n_queries;
+    a.head = c->head;
+    const uint32_t grid = c->ctas < n_queries ? c->ctas : n_queries;
+    cigar_kernel<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? GWFA_OK : GWFA_ERR_CUDA;
+}
