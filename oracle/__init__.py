@@ -19,8 +19,16 @@ Pins (what ties each function to something other than itself; see tests/):
                      exceeds every a.  The tie rules for W~ in pruned mode are
                      a reading of the paper, pinned only by hand-traced cases.
   * levenshtein    - textbook values and a python restatement.
+  * ends variants  - (free walk start / free walk end / no end vertex, Sec. 2.1)
+                     the DP against brute-force enumeration of walks and of
+                     their skipped prefixes / suffixes (brute.py); the variant
+                     Gwfa against the variant DP; closed forms: free start and
+                     end on one vertex is the best substring match, a query
+                     spelled inside a vertex gives 0.
 """
 from __future__ import annotations
+
+FREE_START, FREE_END, EXTEND = 1, 2, 4   # formulation variants (flags)
 
 import ctypes
 import os
@@ -70,6 +78,11 @@ def _load():
             lib.oracle_gwfa.argtypes = [u32, P, P, u64, P, P, P, u64, u32, u32, i64, i64,
                                         ctypes.POINTER(Stats)]
             lib.oracle_gwfa.restype = ctypes.c_int
+            lib.oracle_dp_ends.argtypes = [u32, P, P, u64, P, P, P, u64, u32, u32, ctypes.c_int]
+            lib.oracle_dp_ends.restype = i64
+            lib.oracle_gwfa_ends.argtypes = [u32, P, P, u64, P, P, P, u64, u32, u32, i64, i64, ctypes.c_int,
+                                             ctypes.POINTER(Stats)]
+            lib.oracle_gwfa_ends.restype = ctypes.c_int
             lib.oracle_stats_size.restype = u64
             assert lib.oracle_stats_size() == ctypes.sizeof(Stats)
             _lib = lib
@@ -111,32 +124,37 @@ def levenshtein(x: bytes, y: bytes) -> int:
     return int(lib.oracle_levenshtein(px, len(ax), py, len(ay)))
 
 
-def dp_distance(g, q: bytes, v_s: int, v_e: int) -> int:
-    """Eq. 1 distance (negative = error status)."""
+def dp_distance(g, q: bytes, v_s: int, v_e: int, ends: int = 0) -> int:
+    """Eq. 1 distance (negative = error status); `ends` = variant flags."""
     lib = _load()
     ga = _gargs(g)
     aq, pq = _buf(q)
+    if ends:
+        return int(lib.oracle_dp_ends(*ga.args(), pq, len(aq), v_s, v_e, ends))
     return int(lib.oracle_dp(*ga.args(), pq, len(aq), v_s, v_e))
 
 
-def gwfa(g, q: bytes, v_s: int, v_e: int, a_diff: int = 0, max_score: int = -1) -> dict:
+def gwfa(g, q: bytes, v_s: int, v_e: int, a_diff: int = 0, max_score: int = -1, ends: int = 0) -> dict:
     """Alg. 1-4 on the CPU; returns the distance (or status) and the work counts."""
     lib = _load()
     ga = _gargs(g)
     aq, pq = _buf(q)
     st = Stats()
-    lib.oracle_gwfa(*ga.args(), pq, len(aq), v_s, v_e, a_diff, max_score, ctypes.byref(st))
+    if ends:
+        lib.oracle_gwfa_ends(*ga.args(), pq, len(aq), v_s, v_e, a_diff, max_score, ends, ctypes.byref(st))
+    else:
+        lib.oracle_gwfa(*ga.args(), pq, len(aq), v_s, v_e, a_diff, max_score, ctypes.byref(st))
     return st.as_dict()
 
 
-def gwfa_many(g, queries, idx, a_diff: int = 0, threads: int | None = None) -> list[dict]:
+def gwfa_many(g, queries, idx, a_diff: int = 0, threads: int | None = None, ends: int = 0) -> list[dict]:
     """oracle gwfa over queries[idx] with a thread pool (ctypes releases the GIL)."""
     from concurrent.futures import ThreadPoolExecutor
     ga = _gargs(g)
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(threads) as ex:
         return list(ex.map(lambda i: gwfa(ga, queries.query(int(i)), int(queries.v_s[i]),
-                                          int(queries.v_e[i]), a_diff), idx))
+                                          int(queries.v_e[i]), a_diff, ends=ends), idx))
 
 
 def dp_many(g, queries, idx, threads: int | None = None) -> list[int]:

@@ -75,3 +75,44 @@ def shortest_spelled_walk(labels: list[bytes], arcs: list[tuple[int, int]], vs: 
                 dist[u] = nd
                 heapq.heappush(pq, (nd, u))
     return None
+
+
+def best_walk_distance_ends(labels: list[bytes], arcs: list[tuple[int, int]], q: bytes, vs: int,
+                            ve: int, free_start: bool, free_end: bool, extend: bool) -> int | None:
+    """The formulation variants of Sec. 2.1 by enumeration: min over walks w from vs
+    (ending at ve, or anywhere when `extend`) and over the prefix a of sigma(vs) the
+    walk may skip (free_start) and the suffix b of its last vertex it may skip
+    (free_end or extend) of d(sigma(w)[a : |sigma(w)| - b], q).
+
+    Any walk that extends w by a vertex u aligns a segment of at least
+    |sigma(w)| - a >= |sigma(w)| - |vs| bases (only u's own bases may be skipped at
+    the end), so once |sigma(w)| - |vs| exceeds |q| + best no extension of w can
+    improve on best.
+    """
+    succ: dict[int, list[int]] = {}
+    for u, v in arcs:
+        succ.setdefault(u, []).append(v)
+    best = [None]
+    skip0 = len(labels[vs]) if free_start else 0
+    cap = 2 * len(q) + sum(len(x) for x in labels) + skip0   # before any walk qualifies
+
+    def rec(v: int, spelled: bytes):
+        s = spelled + labels[v]
+        if extend or v == ve:
+            starts = range(len(labels[vs]) + 1) if free_start else [0]
+            ends = range(len(labels[v]) + 1) if (free_end or extend) else [0]
+            for a in starts:
+                for b in ends:
+                    if a > len(s) - b:
+                        continue
+                    d = levenshtein_py(s[a:len(s) - b], q)
+                    if best[0] is None or d < best[0]:
+                        best[0] = d
+        lim = cap if best[0] is None else len(q) + best[0]
+        if len(s) - skip0 > lim:
+            return
+        for u in succ.get(v, []):
+            rec(u, s)
+
+    rec(vs, b"")
+    return best[0]

@@ -19,6 +19,26 @@
  *                       (GwfPrune), in the paper's order, single threaded, with
  *                       a FIFO queue.  It is the reference for pruned distances
  *                       and for the work counts (sum and peak of |Q|).
+ *   oracle_dp_ends,     the same two with the formulation variants Sec. 2.1
+ *   oracle_gwfa_ends    mentions (their details are in a supplement that is not
+ *                       available; these are read off Eq. 1 and Alg. 1):
+ *                         OR_FREE_START  the walk may begin at any position of
+ *                                        v_s: row 0 of Eq. 1 is 0 on every cell
+ *                                        of v_s; Alg. 1 starts from the
+ *                                        diagonals (v_s, -j) with offset j;
+ *                         OR_FREE_END    the walk may end at any position of
+ *                                        v_e: the answer is min_j H_{|q|,ve,j};
+ *                                        Alg. 1 stops at the first score whose
+ *                                        extension puts a diagonal of v_e on
+ *                                        query position |q|;
+ *                         OR_EXTEND      no end vertex: the whole query is
+ *                                        aligned to a walk from v_s that ends
+ *                                        anywhere: min over v, j of H_{|q|,v,j};
+ *                                        Alg. 1 stops when any diagonal reaches
+ *                                        query position |q|.
+ *                       A walk may skip a whole end vertex (j = 0 at v_e is the
+ *                       end of a predecessor).  Pruning is not combined with
+ *                       the variants.
  *
  * Readings of points the paper leaves open (they are the library's readings
  * too, stated once more here so this file stands alone):
@@ -51,6 +71,11 @@
 #define OR_ERR_EMPTY_FRONTIER (-5)
 #define OR_ERR_SCORE_LIMIT (-8)
 #define OR_ERR_OOM (-2)
+
+/* formulation variants (flags) */
+#define OR_FREE_START 1
+#define OR_FREE_END 2
+#define OR_EXTEND 4
 
 static int code_of(char c) {
     switch (c) {
@@ -224,12 +249,15 @@ static int dp_relax_vertex(const og_graph *g, const uint8_t *inS, uint32_t v,
     return changed;
 }
 
-int64_t oracle_dp(uint32_t nv, const char *seq, const uint64_t *seq_off,
-                  uint64_t na, const uint32_t *asrc, const uint32_t *adst,
-                  const char *q, uint64_t n, uint32_t vs, uint32_t ve) {
+int64_t oracle_dp_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
+                       uint64_t na, const uint32_t *asrc, const uint32_t *adst,
+                       const char *q, uint64_t n, uint32_t vs, uint32_t ve, int ends) {
     og_graph g;
+    if (ends & ~(OR_FREE_START | OR_FREE_END | OR_EXTEND)) return OR_ERR_INVALID;
+    const int extend = (ends & OR_EXTEND) != 0;
     int st = og_build(&g, nv, seq, seq_off, na, asrc, adst);
     if (st) return st;
+    if (extend) ve = vs;   /* no end vertex */
     if (vs >= nv || ve >= nv) { og_free(&g); return OR_ERR_INVALID; }
     uint8_t *qc = (uint8_t *)malloc(n ? n : 1);
     for (uint64_t i = 0; i < n; ++i) {
@@ -242,7 +270,8 @@ int64_t oracle_dp(uint32_t nv, const char *seq, const uint64_t *seq_off,
     if (!fw[ve]) { free(fw); free(bw); free(qc); og_free(&g); return OR_ERR_UNREACHABLE; }
     uint8_t *inS = fw;
     uint32_t nS = 0;
-    for (uint32_t v = 0; v < nv; ++v) { inS[v] = fw[v] && bw[v]; nS += inS[v]; }
+    /* S: the vertices on some vs->ve walk; without an end vertex, all reachable ones */
+    for (uint32_t v = 0; v < nv; ++v) { inS[v] = fw[v] && (extend || bw[v]); nS += inS[v]; }
     free(bw);
     uint32_t *Sv = (uint32_t *)malloc((nS ? nS : 1) * sizeof(uint32_t));
     uint8_t *selfl = (uint8_t *)calloc(nv, 1);
@@ -267,6 +296,8 @@ int64_t oracle_dp(uint32_t nv, const char *seq, const uint64_t *seq_off,
     /* row 0: only the initial condition and the in-row cases */
     for (uint64_t c = 0; c < ncol; ++c) prev[c] = OR_INF;
     prev[col[vs]] = 0;
+    if (ends & OR_FREE_START)   /* the walk may begin at any position of vs */
+        for (uint32_t j = 0; j <= og_len(&g, vs); ++j) prev[col[vs] + j] = 0;
     for (;;) {
         int ch = 0;
         for (uint32_t s = 0; s < nS; ++s) ch |= dp_relax_vertex(&g, inS, Sv[s], prev, col, selfl[Sv[s]]);
@@ -300,8 +331,20 @@ int64_t oracle_dp(uint32_t nv, const char *seq, const uint64_t *seq_off,
         int32_t *tt = prev; prev = cur; cur = tt;
     }
     int64_t ans = prev[col[ve] + og_len(&g, ve)];
+    if (extend) {                         /* min over every cell of row |q| */
+        for (uint64_t c = 0; c < ncol; ++c) if (prev[c] < ans) ans = prev[c];
+    } else if (ends & OR_FREE_END) {      /* min over the cells of ve in row |q| */
+        for (uint32_t j = 0; j <= og_len(&g, ve); ++j)
+            if (prev[col[ve] + j] < ans) ans = prev[col[ve] + j];
+    }
     free(Sv); free(col); free(prev); free(cur); free(selfl); free(inS); free(qc); og_free(&g);
     return ans == OR_INF ? OR_ERR_UNREACHABLE : ans;
+}
+
+int64_t oracle_dp(uint32_t nv, const char *seq, const uint64_t *seq_off,
+                  uint64_t na, const uint32_t *asrc, const uint32_t *adst,
+                  const char *q, uint64_t n, uint32_t vs, uint32_t ve) {
+    return oracle_dp_ends(nv, seq, seq_off, na, asrc, adst, q, n, vs, ve, 0);
 }
 
 /* --------------------------------------------------------------------------
@@ -416,14 +459,20 @@ static inline int64_t lcp(const uint8_t *q, int64_t n, int64_t i, const uint8_t 
     return l;
 }
 
-int oracle_gwfa(uint32_t nv, const char *seq, const uint64_t *seq_off,
-                uint64_t na, const uint32_t *asrc, const uint32_t *adst,
-                const char *qs, uint64_t n, uint32_t vs, uint32_t ve,
-                int64_t a_diff, int64_t max_score, oracle_stats *out) {
+int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
+                     uint64_t na, const uint32_t *asrc, const uint32_t *adst,
+                     const char *qs, uint64_t n, uint32_t vs, uint32_t ve,
+                     int64_t a_diff, int64_t max_score, int ends, oracle_stats *out) {
     memset(out, 0, sizeof(*out));
     og_graph g;
+    if ((ends & ~(OR_FREE_START | OR_FREE_END | OR_EXTEND)) || (ends && a_diff > 0)) {
+        out->distance = OR_ERR_INVALID;
+        return OR_ERR_INVALID;
+    }
+    const int extend = (ends & OR_EXTEND) != 0;
     int st = og_build(&g, nv, seq, seq_off, na, asrc, adst);
     if (st) { out->distance = st; return st; }
+    if (extend) ve = vs;   /* no end vertex */
     if (vs >= nv || ve >= nv) { og_free(&g); out->distance = OR_ERR_INVALID; return OR_ERR_INVALID; }
     uint8_t *q = (uint8_t *)malloc(n ? n : 1);
     for (uint64_t i = 0; i < n; ++i) {
@@ -450,6 +499,14 @@ int oracle_gwfa(uint32_t nv, const char *seq, const uint64_t *seq_off,
         e0->j = 0; e0->base = 0; e0->spill_mark = UINT64_MAX;
     }
     if (dv_push(&Q, vs, 0)) { rc = OR_ERR_OOM; goto done; }  /* Q <- [(v_s, 0)] */
+    if (ends & OR_FREE_START) {   /* query position 0 against every position j of vs */
+        for (int32_t j = 1; j <= (int32_t)og_len(&g, vs); ++j) {
+            ent_t *e = hm_insert(&H, dkey(vs, -j));   /* H~_{v_s,-j} <- j */
+            if (!e) { rc = OR_ERR_OOM; goto done; }
+            e->j = j; e->base = 0; e->spill_mark = UINT64_MAX;
+            if (dv_push(&Q, vs, -j)) { rc = OR_ERR_OOM; goto done; }
+        }
+    }
     int64_t d = 0;                                    /* d <- 0 */
     uint64_t ext_call = 0;
     for (;;) {
@@ -497,6 +554,15 @@ int oracle_gwfa(uint32_t nv, const char *seq, const uint64_t *seq_off,
         /* end test of Alg. 1 */
         ent_t *ee = hm_find(&H, dkey(ve, (int32_t)ke));
         if (ee && ee->j == (int32_t)og_len(&g, ve)) break;
+        if (ends & (OR_FREE_END | OR_EXTEND)) {   /* a diagonal just extended reached |q| */
+            int hit = 0;
+            for (uint64_t p = 0; p < Q.n && !hit; ++p) {
+                if (!extend && Q.a[p].v != ve) continue;
+                ent_t *e = hm_find(&H, dkey(Q.a[p].v, Q.a[p].k));
+                hit = (int64_t)Q.a[p].k + e->j == (int64_t)n;
+            }
+            if (hit) break;
+        }
         if (max_score >= 0 && d >= max_score) { rc = OR_ERR_SCORE_LIMIT; goto done; }
         d = d + 1;                                    /* d <- d + 1 */
 
@@ -577,6 +643,13 @@ done:
     if (rc != OR_OK) out->distance = rc;
     free(H.e); free(Hp.e); free(Q.a); free(Qp.a); free(q); og_free(&g);
     return rc;
+}
+
+int oracle_gwfa(uint32_t nv, const char *seq, const uint64_t *seq_off,
+                uint64_t na, const uint32_t *asrc, const uint32_t *adst,
+                const char *qs, uint64_t n, uint32_t vs, uint32_t ve,
+                int64_t a_diff, int64_t max_score, oracle_stats *out) {
+    return oracle_gwfa_ends(nv, seq, seq_off, na, asrc, adst, qs, n, vs, ve, a_diff, max_score, 0, out);
 }
 
 /* size of oracle_stats, so the python wrapper can check its mirror */
