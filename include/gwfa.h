@@ -60,7 +60,22 @@ typedef struct {
                             gwfa_engine_set_paths */
     int32_t max_score;   /* stop with GWFA_ERR_SCORE_LIMIT once d would exceed it; -1 = no limit */
     int32_t wait_limit;  /* serving: iteration limit of device-side waits; 0 = default */
-} gwfa_opts;
+    int32_t ends;        /* formulation variant (Sec. 2.1), GWFA_FREE_* / GWFA_EXTEND flags;
+                            0 = global alignment from the first base of v_s to the last of
+                            v_e (Def. 2).  Needs max_lag == 0; the plain path and the
+                            batch engine take it, the server and gwfa_align_noalloc
+                            refuse it (GWFA_ERR_INVALID) */
+} gwfa_opts;                 /* 20 bytes */
+
+/* Formulation variants: the walk may begin at any position of v_s (its prefix is
+ * skipped at no cost), may end at any position of v_e (its suffix skipped), or
+ * has no end vertex at all -- the whole query is aligned to a walk that starts
+ * at v_s and ends anywhere (v_e is ignored).  A walk may skip a whole end vertex.
+ * The reported distance is the minimum over those walks; with traceback the
+ * walk runs from v_s to the vertex where the alignment ended. */
+#define GWFA_FREE_START 1
+#define GWFA_FREE_END 2
+#define GWFA_EXTEND 4
 
 /*
  * Per-query result.  Work counters follow Alg. 1-3 exactly and are identical
@@ -330,7 +345,10 @@ int gwfa_cigar_destroy(gwfa_cigar *c);
  *   d_cigar           n_queries * cigar_cap operations; query i writes from
  *                     d_cigar[i * cigar_cap]
  *   d_out             n_queries results
- * Calls on one gwfa_cigar share its workspace: order them on one stream.
+ * Calls on one gwfa_cigar share its workspace: order them on one stream.  The
+ * alignment is global over the whole spelled walk, so it is meant for batches
+ * aligned with ends = 0 (a walk of a free-end variant may cost more than d
+ * globally: GWFA_ERR_SCORE_LIMIT).
  */
 int gwfa_cigar_device(gwfa_cigar *c, uint32_t n_queries, const uint32_t *d_words,
                       const uint64_t *d_q_off, const gwfa_result *d_res, const uint32_t *d_paths,

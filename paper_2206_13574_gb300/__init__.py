@@ -43,7 +43,11 @@ CIGAR_CHARS = {GWFA_CIGAR_INS: "I", GWFA_CIGAR_DEL: "D", GWFA_CIGAR_EQ: "=", GWF
 
 class gwfa_opts(ctypes.Structure):
     _fields_ = [("max_lag", ctypes.c_int32), ("traceback", ctypes.c_int32),
-                ("max_score", ctypes.c_int32), ("wait_limit", ctypes.c_int32)]
+                ("max_score", ctypes.c_int32), ("wait_limit", ctypes.c_int32), ("ends", ctypes.c_int32)]
+
+
+# formulation variants (gwfa_opts.ends flags)
+GWFA_FREE_START, GWFA_FREE_END, GWFA_EXTEND = 1, 2, 4
 
 
 class gwfa_result(ctypes.Structure):
@@ -200,8 +204,8 @@ def _c(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
-def _opts(max_lag: int, max_score: int, traceback: int = 0) -> gwfa_opts:
-    return gwfa_opts(int(max_lag), int(traceback), int(max_score), 0)
+def _opts(max_lag: int, max_score: int, traceback: int = 0, ends: int = 0) -> gwfa_opts:
+    return gwfa_opts(int(max_lag), int(traceback), int(max_score), 0, int(ends))
 
 
 class Graph:
@@ -229,19 +233,21 @@ class Graph:
         _check(load().gwfa_graph_get_info(self.handle, ctypes.byref(i)), "gwfa_graph_get_info")
         return {k: int(getattr(i, k)) for k, _ in i._fields_}
 
-    def align(self, q: bytes, v_s: int, v_e: int, max_lag: int = 0, max_score: int = -1) -> dict:
+    def align(self, q: bytes, v_s: int, v_e: int, max_lag: int = 0, max_score: int = -1,
+              ends: int = 0) -> dict:
         """Plain path (gwfa_align): one query, one kernel launch, synchronous."""
         r = gwfa_result()
-        o = _opts(max_lag, max_score)
+        o = _opts(max_lag, max_score, 0, ends)
         qb = bytes(q)
         _check(load().gwfa_align(self.handle, qb, len(qb), v_s, v_e, ctypes.byref(o), ctypes.byref(r)),
                "gwfa_align")
         return r.as_dict()
 
-    def align_path(self, q: bytes, v_s: int, v_e: int, max_score: int = -1, path_cap: int = 1 << 16):
+    def align_path(self, q: bytes, v_s: int, v_e: int, max_score: int = -1, path_cap: int = 1 << 16,
+                   ends: int = 0):
         """(result, walk) with the optimal walk's vertex ids (gwfa_align_path)."""
         r = gwfa_result()
-        o = _opts(0, max_score)
+        o = _opts(0, max_score, 0, ends)
         qb = bytes(q)
         path = np.zeros(path_cap, dtype=np.uint32)
         plen = _u32()
@@ -305,7 +311,7 @@ class Engine:
 
     def align_batch(self, seq, off, v_s, v_e, order=None, max_lag: int = 0, max_score: int = -1,
                     stream: int = 0, out: np.ndarray | None = None, n_wide: int = 0,
-                    n_huge: int = 0) -> np.ndarray:
+                    n_huge: int = 0, ends: int = 0) -> np.ndarray:
         """Host buffers in, host results out (gwfa_align_batch)."""
         seq = _c(seq, np.uint8)
         off = _c(off, np.uint64)
@@ -313,7 +319,7 @@ class Engine:
         ve = _c(v_e, np.uint32)
         n = len(vs)
         res = out if out is not None else np.zeros(n, dtype=RESULT_DTYPE)
-        o = _opts(max_lag, max_score)
+        o = _opts(max_lag, max_score, 0, ends)
         od = None if order is None else _c(order, np.uint32)
         _check(load().gwfa_align_batch(self.handle, n, seq.ctypes.data, off.ctypes.data, vs.ctypes.data,
                                        ve.ctypes.data, None if od is None else od.ctypes.data,
@@ -325,9 +331,9 @@ class Engine:
     def align_batch_device(self, n: int, d_words: int, d_q_off: int, d_v_s: int, d_v_e: int,
                            d_order: int | None, d_status: int | None, d_out: int,
                            max_lag: int = 0, max_score: int = -1, stream: int = 0, n_wide: int = 0,
-                           traceback: bool = False, n_huge: int = 0):
+                           traceback: bool = False, n_huge: int = 0, ends: int = 0):
         """Device pointers in and out, asynchronous on `stream` (gwfa_align_batch_device)."""
-        o = _opts(max_lag, max_score, int(traceback))
+        o = _opts(max_lag, max_score, int(traceback), ends)
         _check(load().gwfa_align_batch_device(self.handle, n, d_words, d_q_off, d_v_s, d_v_e,
                                               d_order or None, _sched(n_huge, n_wide), d_status or None,
                                               ctypes.byref(o),
@@ -379,14 +385,14 @@ class DeviceBatch:
                             self.status.data_ptr(), st.cuda_stream)
 
     def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None, n_wide: int = 0,
-            traceback: bool = False, n_huge: int = 0):
+            traceback: bool = False, n_huge: int = 0, ends: int = 0):
         import torch
         st = stream if stream is not None else torch.cuda.current_stream(self.q.device)
         engine.align_batch_device(self.n, self.words.data_ptr(), self.q_off.data_ptr(),
                                   self.v_s.data_ptr(), self.v_e.data_ptr(),
                                   None if self.order is None else self.order.data_ptr(),
                                   self.status.data_ptr(), self.out.data_ptr(), max_lag, max_score,
-                                  st.cuda_stream, n_wide, traceback, n_huge)
+                                  st.cuda_stream, n_wide, traceback, n_huge, ends)
 
     def results(self) -> np.ndarray:
         return self.out.cpu().numpy().view(RESULT_DTYPE)

@@ -217,6 +217,11 @@ static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_
                        const gwfa_opts &o, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
                        uint32_t *path_len);
 
+// formulation variant flags: known bits only, and not combined with pruning
+static bool ends_ok(const gwfa_opts &o) {
+    return (o.ends & ~(GWFA_FREE_START | GWFA_FREE_END | GWFA_EXTEND)) == 0 && (o.ends == 0 || o.max_lag == 0);
+}
+
 int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
                const gwfa_opts *opts, gwfa_result *out) {
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
@@ -240,8 +245,9 @@ static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_
     memset(out, 0, sizeof(*out));
     out->edit_distance = -1;
     if (path_len) *path_len = 0;
+    if (o.ends & GWFA_EXTEND) ve = vs;   // no end vertex
     if (vs >= g->nv || ve >= g->nv || o.max_lag < 0 || n >= 0x7FFFFFFFu ||
-        (o.traceback && o.max_lag != 0)) {
+        (o.traceback && o.max_lag != 0) || !ends_ok(o)) {
         out->status = GWFA_ERR_INVALID;
         return GWFA_ERR_INVALID;
     }
@@ -311,6 +317,7 @@ static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_
         a.max_lag = o.max_lag;
         a.max_score = o.max_score;
         a.traceback = o.traceback ? 1 : 0;
+        a.ends = o.ends;
         a.paths = o.traceback ? d_path : nullptr;
         a.path_len = o.traceback ? d_plen : nullptr;
         a.path_cap = path_cap;
@@ -539,6 +546,7 @@ static TierArgs tier_args(gwfa_engine *e, const uint32_t *d_words, const uint64_
     a.max_score = o.max_score;
     a.stats = e->stats;
     a.traceback = o.traceback ? 1 : 0;
+    a.ends = o.ends;
     a.paths = e->paths;
     a.path_len = e->path_len;
     a.path_cap = e->path_cap;
@@ -653,7 +661,7 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
                             const gwfa_opts *opts, gwfa_result *d_out, void *stream) {
     if (!e || !d_words || !d_q_off || !d_vs || !d_ve || !d_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0)) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0) || !ends_ok(o)) return GWFA_ERR_INVALID;
     if ((o.max_lag > 0 || o.traceback) && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
     if (n == 0) return GWFA_OK;
     std::lock_guard<std::mutex> lk(e->mu);
@@ -670,7 +678,7 @@ int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t
                      const gwfa_schedule *sched, const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
     if (!e || !h_q_off || !h_vs || !h_ve || !h_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0)) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0) || !ends_ok(o)) return GWFA_ERR_INVALID;
     if ((o.max_lag > 0 || o.traceback) && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
     if (n == 0) return GWFA_OK;
     if (h_q_off[0] != 0) return GWFA_ERR_INVALID;

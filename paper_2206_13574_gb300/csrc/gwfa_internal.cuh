@@ -109,6 +109,7 @@ struct TierArgs {
     unsigned long long *stats;  // optional, kStatWords per query id (see gwfa_engine_set_stats)
     int q_smem;                 // query words are in shared memory (server kernel)
     int traceback;              // 64-bit values carry a trace index (Alg. 5-6) instead of a base
+    int ends;                   // formulation variant flags (GWFA_FREE_START / _FREE_END / _EXTEND)
     uint32_t *paths;            // traceback: path_cap vertex ids per query id
     uint32_t *path_len;         // traceback: walk length per query id (may exceed path_cap)
     uint32_t path_cap;

@@ -104,7 +104,7 @@ struct Sh {
     uint32_t peak;
     uint32_t claim[3];  // work counters of the phases, rotating (see align_one)
     uint32_t tlen;      // traceback: entries of T
-    uint32_t end_payload;
+    unsigned long long end_vp;   // traceback: vertex << 32 | trace of a diagonal at the end point
 };
 
 __device__ __forceinline__ void set_err(Sh &sh, int code) { atomicCAS(&sh.err, 0, code); }
@@ -141,7 +141,18 @@ struct QCtx {
     uint32_t ve;
     int ke;
     bool smem;            // qw points to shared memory (server kernel)
+    bool free_end;        // the walk may end at any position of v_e (or anywhere: any_v)
+    bool any_v;           // no end vertex
 };
+
+// End test of Alg. 1 on a diagonal just extended to offset j: the point (k + j, j)
+// of v is the end point (|q|, |v_e|) of v_e; with a free walk end, any point of
+// v_e on query position |q|; without an end vertex, any such point.
+__device__ __forceinline__ bool at_end(const QCtx &q, uint32_t v, int k, int j, uint32_t lv) {
+    if (k + j != q.n) return false;
+    if (q.any_v) return true;
+    return v == q.ve && (q.free_end || (uint32_t)j == lv);
+}
 
 // 16 query bases from position p: read-only cache for a batch staged before the
 // launch, plain (shared-memory) loads for a query the CTA staged itself.
@@ -290,7 +301,7 @@ __device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const
         } else {
             set_err(sh, GWFA_ERR_CAPACITY);
         }
-        if (u == q.ve && k == q.ke && (uint32_t)l == vi.y) sh.found = 1;
+        if (at_end(q, u, k, l, vi.y)) sh.found = 1;
         if ((uint32_t)l == vi.y) {
             a0 = vi.z;
             a1 = vi.w;
@@ -355,7 +366,7 @@ __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &
             if (live[u]) {
                 val[u] += lcp_finish(q, k[u] + val[u], g.words + vi[u].x, val[u], maxl[u], x[u]);
                 __stcg(&s.slots[ent[u].slot].vals[ln], val[u]);
-                if (ent[u].v == q.ve && k[u] == q.ke && (uint32_t)val[u] == vi[u].y) sh.found = 1;
+                if (at_end(q, ent[u].v, k[u], val[u], vi[u].y)) sh.found = 1;
             }
             const uint32_t ei = eidx + u;
             if (ei < s.cap) {
@@ -421,9 +432,11 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
             const int j2 = j + lcp(q, i, g.words + vi.x, j, (int)vi.y);
             val = pk(j2, kTagSettled, pbase(val));
             __stcg(&s.slots[ent.slot].vals[ln], val);
-            if (ent.v == q.ve && k == q.ke && (uint32_t)j2 == vi.y) {
+            if (at_end(q, ent.v, k, j2, vi.y)) {
                 sh.found = 1;
-                sh.end_payload = pbase(val);
+                // one 64-bit store, so that the vertex and its trace stay a pair when
+                // several diagonals reach a free end in the same score
+                sh.end_vp = ((unsigned long long)ent.v << 32) | pbase(val);
             }
             a = (unsigned long long)(k + j2) + pbase(val) + (unsigned)j2;   // a = i + W~ (Alg. 4)
             if ((uint32_t)j2 == vi.y) {
@@ -600,6 +613,9 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
     q.ve = A.v_e[qid];
     int pre = 0;
     if (A.qstatus) pre = A.qstatus[qid];
+    q.any_v = (A.ends & GWFA_EXTEND) != 0;
+    q.free_end = (A.ends & (GWFA_FREE_END | GWFA_EXTEND)) != 0;
+    if (q.any_v) q.ve = vs;   // no end vertex: v_e is not read
     if (!pre && (vs >= g.nv || q.ve >= g.nv)) pre = GWFA_ERR_INVALID;
     if (pre) {
         if (threadIdx.x == 0) {
@@ -622,7 +638,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         sh.nq[0] = sh.nq[1] = 0;
         sh.claim[0] = sh.claim[1] = sh.claim[2] = 0;
         sh.tlen = 0;
-        sh.end_payload = kNoTrace;
+        sh.end_vp = ((unsigned long long)q.ve << 32) | kNoTrace;
         const int slot = find_or_insert(s, sh, tile_key(vs, 0));
         if (slot >= 0) {
             typename VT<P>::T v0;
@@ -634,6 +650,29 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         }
     }
     __syncthreads();
+    if (A.ends & GWFA_FREE_START) {
+        // free walk start (Sec. 2.1 variant): query position 0 also faces every
+        // position j of v_s, i.e. the diagonals (v_s, -j) start with offset j
+        const int lvs = (int)__ldg(&g.vinfo[vs]).y;
+        const int ntile = (lvs + kTile - 1) / kTile;   // tiles kb = -1 .. -ntile
+        for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+            const int kb = -1 - t;
+            uint32_t bits = 0;
+            for (int ln = 0; ln < kTile; ++ln)
+                if (kb * kTile + ln >= -lvs) bits |= 1u << ln;
+            const int slot = find_or_insert(s, sh, tile_key(vs, kb));
+            if (slot < 0) continue;
+            for (int ln = 0; ln < kTile; ++ln) {
+                if (!((bits >> ln) & 1u)) continue;
+                const int j = -(kb * kTile + ln);
+                if constexpr (P) s.slots[slot].vals[ln] = pk(j, kTagFresh, A.traceback ? kNoTrace : 0u);
+                else s.slots[slot].vals[ln] = j;
+            }
+            atomicAdd(&sh.visited, (unsigned long long)__popc(bits));
+            reg_append(&s.slots[slot].reg[1], s.qlist, &sh.nq[0], s.cap, (uint32_t)slot, vs, kb, bits, sh);
+        }
+        __syncthreads();
+    }
 
     uint32_t phase = 1;   // parity (phase & 1) of the reg words of the tiles in Q
     uint32_t cstep = 0;   // processing phases so far: phase number c claims with claim[c % 3]
@@ -754,7 +793,8 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                 if (A.traceback && status == 0) {
                     // GwfTraceback (Alg. 6): push the end vertex, then follow T back to the
                     // start and write the walk in order
-                    const uint32_t te = push_trace(s, sh, q.ve, sh.end_payload);
+                    const uint32_t te = push_trace(s, sh, (uint32_t)(sh.end_vp >> 32),
+                                                   (uint32_t)sh.end_vp & 0xFFFFFFFFu);
                     uint32_t len = 0;
                     for (uint32_t t = te; t != kNoTrace && len <= sh.tlen; t = __ldcg(&s.trace[t]).y) ++len;
                     if (A.path_len) A.path_len[qid] = len;
