@@ -96,6 +96,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_queries(g, qs, rank: int):
+    """Rank r's batch under weak scaling: rank 0 aligns the config-2 batch itself, rank
+    r > 0 a batch of the same size and length / divergence distribution drawn with
+    query seed 2 + 1000 r on the same graph, so every rank processes its own units."""
+    if rank == 0:
+        return qs
+    from paper_2206_13574_gb300 import synth
+    c = synth.CONFIGS[2]
+    return synth.make_queries(g, len(qs), 2 + 1000 * rank, c["length"], c["div"], c["weights"], c["loops"])
+
+
+def reduce_ranks(t_step: float, t_e2e: float, aligned_bp: int, cells: int, device) -> tuple:
+    """Whole-job figures over the ranks: the slowest rank's step times (MAX) and the
+    units all ranks processed (SUM).  One process: the inputs unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_step, t_e2e, aligned_bp, cells
+    t = torch.tensor([t_step, t_e2e], dtype=torch.float64, device=device)
+    u = torch.tensor([aligned_bp, cells], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(u[0]), int(u[1])
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -307,6 +332,8 @@ def main():
     dev = torch.device("cuda", local)
     _build.build()
 
+    qs = rank_queries(g, qs, rank)
+    total_bp = int(qs.lengths().sum())
     graph = gw.Graph.from_synth(g, device=local)
     eng = gw.Engine(graph)
     # longest queries first (a plain length-sorted schedule); the longest go to wide CTAs
@@ -350,11 +377,6 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     t_step = float(np.mean(times))
-    if ws > 1:
-        t = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = aligned_bp * ws / t_step / 1e9
 
     # end to end through the host-buffer entry point, inputs in pinned host memory
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -392,6 +414,9 @@ def main():
     d2h = len(qs) * gw.RESULT_DTYPE.itemsize
 
     cells = int(res["cells"][ok].sum())
+    # every rank's units and the slowest rank's times make the whole-job figures
+    t_step, t_e2e, job_bp, job_cells = reduce_ranks(t_step, t_e2e, aligned_bp, cells, dev)
+    value = job_bp / t_step / 1e9
     # algorithmic bytes of the hot path: per live diagonal and score, the offset is
     # read and written by GwfExtend (8 B) and read again plus up to three candidate
     # offsets written by GwfExpand (16 B); every aligned base is read once from the
@@ -436,7 +461,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "queries": len(qs), "bases": total_bp,
-                       "aligned_bases": aligned_bp, "cells": cells,
+                       "aligned_bases": job_bp, "cells": job_cells,
+                       "per_rank": "queries / bases are one rank's batch; aligned_bases and cells sum all ranks",
                        "parallelism": f"query-sharded x{ws} (replicated graph)",
                        "l2": "flushed (256 MB write) before every timed step",
                        "schedule": "longest query first", "n_wide": n_wide,
@@ -447,9 +473,9 @@ def main():
                            for t in range(eng.config.n_tiers)],
                        "threads_per_cta": eng.config.threads,
                        "ok_queries": int(ok.sum())},
-            "e2e": {"value": aligned_bp * ws / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_bp / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches_per_step * args.steps * ws,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (tpc * cells) if tpc is not None else None,
@@ -459,7 +485,7 @@ def main():
                          "peak_kind": f"{peak_kind} HBM copy",
                          "kernel": "align_kernel<exact> (all tiers of one step)",
                          "bytes_per_cell": B_CELL},
-            "cells_per_s": cells * ws / t_step,
+            "cells_per_s": job_cells / t_step,
             "clocks": clk,
             "cpu_baseline": cpu,
             "plain": plain,
