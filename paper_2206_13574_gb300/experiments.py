@@ -3,6 +3,7 @@
     python -m paper_2206_13574_gb300.experiments config3     # cyclic graph: exact vs lag-pruned
     python -m paper_2206_13574_gb300.experiments scheduler   # large graph: learned vs plain scheduling
     python -m paper_2206_13574_gb300.experiments serving     # server vs one-query-at-a-time
+    python -m paper_2206_13574_gb300.experiments serving5    # the same on the 50 Mb graph (config 5)
 
 Each prints one JSON line.  Inputs are the seeded synthetic workloads of synth.py.
 """
@@ -72,7 +73,7 @@ def config3(n_pruned: int = 2000, n_exact: int = 200, a_diff: int = 1000) -> dic
             "work_ratio_exact_over_pruned": float(ex["cells"][ok].sum() / max(prs["cells"][ok].sum(), 1))}
 
 
-def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300) -> dict:
+def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_plain: int = 100) -> dict:
     """Large graph (50 Mb, lognormal 1-100 kb queries, 0.1-10% divergence), exact:
     plain schedules (input order, longest first) against the learned plan of a cost
     model trained on config-2 and config-3-graph logs (other graphs)."""
@@ -158,6 +159,17 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300) -> d
     top = np.argsort(-ref["device_us"].astype(np.float64))[:8]
     out["slowest_queries"] = [{"len": int(q4.lengths()[i]), "us": int(ref["device_us"][i]),
                                "cells": int(ref["cells"][i]), "visited": int(ref["visited"][i])} for i in top]
+    # S4 on the same workload: the plain path, one synchronous launch per query
+    rng = np.random.default_rng(4)
+    sidx = rng.choice(len(q4), size=min(n_plain, len(q4)), replace=False)
+    t0 = time.perf_counter()
+    for i in sidx:
+        r = gr4.align(q4.query(int(i)), int(q4.v_s[i]), int(q4.v_e[i]))
+        assert r["edit_distance"] == int(ref["edit_distance"][i])
+    tp = time.perf_counter() - t0
+    out["plain_per_query"] = {"queries": int(len(sidx)), "s": tp,
+                              "gbp_per_s": float(q4.lengths()[sidx].sum()) / tp / 1e9,
+                              "ms_per_query": tp / len(sidx) * 1e3}
     out["cells"] = int(ref["cells"].sum())
     out["spearman_pred_cells"] = costmodel.spearman(pred[:, 3], np.log1p(ref["cells"].astype(np.float64)))
     out["r2_log_cells"] = float(costmodel.r2(pred[:, 3:4], np.log1p(ref["cells"].astype(np.float64))[:, None])[0])
@@ -165,16 +177,20 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300) -> d
 
 
 def serving(n_pool: int = 3000, rates=(1000.0, 5000.0, 20000.0), duration: float = 1.0,
-            plain_rate: float = 100.0, plain_duration: float = 2.0) -> dict:
-    """Config-2 graph resident, Poisson arrivals: the continuous-batching server's
-    p50/p99 at several rates, and the plain one-query-at-a-time path at a low rate."""
+            plain_rate: float = 100.0, plain_duration: float = 2.0, cfg: int = 2) -> dict:
+    """A resident graph, Poisson arrivals: the continuous-batching server's p50/p99 at
+    several rates, and the plain one-query-at-a-time path at a low rate.  cfg 2: the
+    config-2 graph and queries; cfg 5: the 50 Mb config-4 graph with its lognormal
+    1-100 kb queries at 0.1-10% divergence."""
     import paper_2206_13574_gb300 as gw
     from paper_2206_13574_gb300 import serving as sv
     from paper_2206_13574_gb300 import synth
-    g, qs = synth.make_config(2, n_queries=n_pool)
+    g, qs = synth.make_config(cfg, n_queries=n_pool)
     graph = gw.Graph.from_synth(g)
     srv = gw.Server(graph)
-    out = {"workload": "config2 graph, config-2 queries, Poisson arrivals"}
+    out = {"workload": ("config2 graph, config-2 queries" if cfg == 2 else
+                        "config5: 50 Mb config-4 graph resident, lognormal 1-100 kb queries, 0.1-10% divergence")
+                       + ", Poisson arrivals"}
     for lam in rates:
         arr = synth.poisson_arrivals(lam, duration, seed=int(lam))
         idx = np.arange(len(arr)) % n_pool
@@ -195,6 +211,8 @@ if __name__ == "__main__":
     b.build()
     which = sys.argv[1] if len(sys.argv) > 1 else "config3"
     t0 = time.time()
-    res = {"config3": config3, "scheduler": scheduler, "serving": serving}[which]()
+    res = {"config3": config3, "scheduler": scheduler, "serving": serving,
+           "serving5": lambda: serving(n_pool=2000, rates=(250.0, 1000.0, 4000.0), duration=1.0,
+                                       plain_rate=10.0, plain_duration=3.0, cfg=5)}[which]()
     res["wall_s"] = time.time() - t0
     print(json.dumps(res))
