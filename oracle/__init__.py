@@ -19,6 +19,10 @@ Pins (what ties each function to something other than itself; see tests/):
                      exceeds every a.  The tie rules for W~ in pruned mode are
                      a reading of the paper, pinned only by hand-traced cases.
   * levenshtein    - textbook values and a python restatement.
+  * memory bound   - (evict_lag) removes H~ entries behind the lag: pinned by the
+                     upper-bound property (never below the exact distance), by
+                     equality with the unbounded run when evict_lag exceeds every
+                     a, and by fewer entries kept at the end.
   * ends variants  - (free walk start / free walk end / no end vertex, Sec. 2.1)
                      the DP against brute-force enumeration of walks and of
                      their skipped prefixes / suffixes (brute.py); the variant
@@ -57,7 +61,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("distance", ctypes.c_int64), ("is_upper_bound", ctypes.c_int64),
                 ("n_scores", ctypes.c_int64), ("cells", ctypes.c_int64),
                 ("peak", ctypes.c_int64), ("visited", ctypes.c_int64),
-                ("pruned", ctypes.c_int64), ("spills", ctypes.c_int64)]
+                ("pruned", ctypes.c_int64), ("spills", ctypes.c_int64), ("evicted", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -83,6 +87,9 @@ def _load():
             lib.oracle_gwfa_ends.argtypes = [u32, P, P, u64, P, P, P, u64, u32, u32, i64, i64, ctypes.c_int,
                                              ctypes.POINTER(Stats)]
             lib.oracle_gwfa_ends.restype = ctypes.c_int
+            lib.oracle_gwfa_ex.argtypes = [u32, P, P, u64, P, P, P, u64, u32, u32, i64, i64, ctypes.c_int,
+                                           i64, i64, ctypes.POINTER(Stats)]
+            lib.oracle_gwfa_ex.restype = ctypes.c_int
             lib.oracle_stats_size.restype = u64
             assert lib.oracle_stats_size() == ctypes.sizeof(Stats)
             _lib = lib
@@ -134,27 +141,35 @@ def dp_distance(g, q: bytes, v_s: int, v_e: int, ends: int = 0) -> int:
     return int(lib.oracle_dp(*ga.args(), pq, len(aq), v_s, v_e))
 
 
-def gwfa(g, q: bytes, v_s: int, v_e: int, a_diff: int = 0, max_score: int = -1, ends: int = 0) -> dict:
-    """Alg. 1-4 on the CPU; returns the distance (or status) and the work counts."""
+def gwfa(g, q: bytes, v_s: int, v_e: int, a_diff: int = 0, max_score: int = -1, ends: int = 0,
+         evict_lag: int = 0, evict_every: int = 0) -> dict:
+    """Alg. 1-4 on the CPU; returns the distance (or status) and the work counts.
+    evict_lag > 0 (with a_diff > 0) bounds H~: every evict_every scores the entries
+    outside Q lagging a_max by evict_lag or more are removed."""
     lib = _load()
     ga = _gargs(g)
     aq, pq = _buf(q)
     st = Stats()
-    if ends:
+    if evict_lag:
+        lib.oracle_gwfa_ex(*ga.args(), pq, len(aq), v_s, v_e, a_diff, max_score, ends, evict_lag, evict_every,
+                           ctypes.byref(st))
+    elif ends:
         lib.oracle_gwfa_ends(*ga.args(), pq, len(aq), v_s, v_e, a_diff, max_score, ends, ctypes.byref(st))
     else:
         lib.oracle_gwfa(*ga.args(), pq, len(aq), v_s, v_e, a_diff, max_score, ctypes.byref(st))
     return st.as_dict()
 
 
-def gwfa_many(g, queries, idx, a_diff: int = 0, threads: int | None = None, ends: int = 0) -> list[dict]:
+def gwfa_many(g, queries, idx, a_diff: int = 0, threads: int | None = None, ends: int = 0,
+              evict_lag: int = 0, evict_every: int = 0) -> list[dict]:
     """oracle gwfa over queries[idx] with a thread pool (ctypes releases the GIL)."""
     from concurrent.futures import ThreadPoolExecutor
     ga = _gargs(g)
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(threads) as ex:
         return list(ex.map(lambda i: gwfa(ga, queries.query(int(i)), int(queries.v_s[i]),
-                                          int(queries.v_e[i]), a_diff, ends=ends), idx))
+                                          int(queries.v_e[i]), a_diff, ends=ends, evict_lag=evict_lag,
+                                          evict_every=evict_every), idx))
 
 
 def dp_many(g, queries, idx, threads: int | None = None) -> list[int]:

@@ -446,9 +446,11 @@ typedef struct {
     int64_t n_scores;      /* number of GwfExtend calls = d + 1 on success */
     int64_t cells;         /* sum over scores of |Q| after GwfExtend */
     int64_t peak;          /* max over scores of |Q| after GwfExtend */
-    int64_t visited;       /* |H~| at return: distinct diagonals ever inserted */
+    int64_t visited;       /* insertions into H~ (= distinct diagonals ever inserted
+                              unless eviction removed some and they came back) */
     int64_t pruned;        /* diagonals dropped by GwfPrune, summed over scores */
     int64_t spills;        /* diagonals inserted by GwfExtend's arc loop */
+    int64_t evicted;       /* entries removed from H~ by the memory bound (evict_lag) */
 } oracle_stats;
 
 /* LCP(q[i+1..|q|], v[j+1..|v|]) in the paper's 1-based notation */
@@ -459,13 +461,23 @@ static inline int64_t lcp(const uint8_t *q, int64_t n, int64_t i, const uint8_t 
     return l;
 }
 
-int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
-                     uint64_t na, const uint32_t *asrc, const uint32_t *adst,
-                     const char *qs, uint64_t n, uint32_t vs, uint32_t ve,
-                     int64_t a_diff, int64_t max_score, int ends, oracle_stats *out) {
+/* Memory-bounded H~ (with pruning only): every evict_every scores, right after
+ * GwfExpand, the entries that are not in the new Q and whose anti-diagonal
+ * a = i + W~ (Alg. 4's measure) lags this score's a_max by evict_lag or more are
+ * removed from H~.  A removed diagonal may be inserted again later (it counts as a
+ * new insertion); every offset is still that of a realised alignment, so the
+ * distance stays an upper bound of the exact one. */
+#define KEEP_MARK (UINT64_MAX - 1)
+
+int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
+                   uint64_t na, const uint32_t *asrc, const uint32_t *adst,
+                   const char *qs, uint64_t n, uint32_t vs, uint32_t ve,
+                   int64_t a_diff, int64_t max_score, int ends, int64_t evict_lag, int64_t evict_every,
+                   oracle_stats *out) {
     memset(out, 0, sizeof(*out));
     og_graph g;
-    if ((ends & ~(OR_FREE_START | OR_FREE_END | OR_EXTEND)) || (ends && a_diff > 0)) {
+    if ((ends & ~(OR_FREE_START | OR_FREE_END | OR_EXTEND)) || (ends && a_diff > 0) ||
+        evict_lag < 0 || (evict_lag > 0 && (a_diff <= 0 || evict_every <= 0))) {
         out->distance = OR_ERR_INVALID;
         return OR_ERR_INVALID;
     }
@@ -488,6 +500,7 @@ int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
     if (!reach) { free(q); og_free(&g); out->distance = OR_ERR_UNREACHABLE; return OR_ERR_UNREACHABLE; }
 
     hmap H = {0}, Hp = {0};
+    int64_t inserted = 0;   /* insertions into H~ */
     dvec Q = {0}, Qp = {0};
     int rc = OR_OK;
     if (hm_init(&H, 1 << 12) || hm_init(&Hp, 1 << 12)) { rc = OR_ERR_OOM; goto done; }
@@ -496,6 +509,7 @@ int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
     int64_t ke = (int64_t)n - og_len(&g, ve);        /* k_e <- |q| - |v_e| */
     {
         ent_t *e0 = hm_insert(&H, dkey(vs, 0));     /* H~_{v_s,0} <- 0 */
+        ++inserted;
         e0->j = 0; e0->base = 0; e0->spill_mark = UINT64_MAX;
     }
     if (dv_push(&Q, vs, 0)) { rc = OR_ERR_OOM; goto done; }  /* Q <- [(v_s, 0)] */
@@ -503,6 +517,7 @@ int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
         for (int32_t j = 1; j <= (int32_t)og_len(&g, vs); ++j) {
             ent_t *e = hm_insert(&H, dkey(vs, -j));   /* H~_{v_s,-j} <- j */
             if (!e) { rc = OR_ERR_OOM; goto done; }
+            ++inserted;
             e->j = j; e->base = 0; e->spill_mark = UINT64_MAX;
             if (dv_push(&Q, vs, -j)) { rc = OR_ERR_OOM; goto done; }
         }
@@ -535,6 +550,7 @@ int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
                     if (!t) {                         /* H~_{u,k+|v|} not in H~ */
                         t = hm_insert(&H, dkey(u, ku));
                         if (!t) { rc = OR_ERR_OOM; goto done; }
+                        ++inserted;
                         t->j = 0;                     /* H~_{u,k+|v|} <- 0 */
                         t->base = base + lv;
                         t->spill_mark = mark;
@@ -567,8 +583,8 @@ int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
         d = d + 1;                                    /* d <- d + 1 */
 
         /* ---- GwfPrune (Alg. 4), between d <- d+1 and GwfExpand ---- */
+        int64_t amax = 0;
         if (a_diff > 0) {
-            int64_t amax = 0;
             for (uint64_t p = 0; p < Q.n; ++p) {
                 ent_t *e = hm_find(&H, dkey(Q.a[p].v, Q.a[p].k));
                 int64_t i = Q.a[p].k + (int64_t)e->j;
@@ -631,18 +647,49 @@ int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
             if (!th) {
                 th = hm_insert(&H, dkey(Qp.a[p].v, Qp.a[p].k));
                 if (!th) { rc = OR_ERR_OOM; goto done; }
+                ++inserted;
             }
             th->j = tp->j; th->base = tp->base; th->spill_mark = UINT64_MAX;
         }
         { dvec tq = Q; Q = Qp; Qp = tq; }            /* Q <- Q' */
         if (Q.n == 0) { rc = OR_ERR_EMPTY_FRONTIER; goto done; }
+
+        /* ---- memory bound on H~ (see above) ---- */
+        if (evict_lag > 0 && d % evict_every == 0) {
+            for (uint64_t p = 0; p < Q.n; ++p) hm_find(&H, dkey(Q.a[p].v, Q.a[p].k))->spill_mark = KEEP_MARK;
+            hmap H2 = {0};
+            if (hm_init(&H2, H.cap)) { rc = OR_ERR_OOM; goto done; }
+            for (uint64_t x = 0; x < H.cap; ++x) {
+                ent_t *e = &H.e[x];
+                if (e->key == EMPTY_KEY) continue;
+                int64_t k = (int32_t)(uint32_t)(e->key & 0xFFFFFFFFu);
+                int64_t a = (k + e->j) + (e->base + e->j);   /* i + W~ */
+                if (e->spill_mark == KEEP_MARK || amax - a < evict_lag) {
+                    ent_t *c = hm_insert(&H2, e->key);
+                    if (!c) { free(H2.e); rc = OR_ERR_OOM; goto done; }
+                    *c = *e;
+                    c->spill_mark = UINT64_MAX;
+                } else {
+                    out->evicted++;
+                }
+            }
+            free(H.e);
+            H = H2;
+        }
     }
     out->distance = d;
 done:
-    out->visited = (int64_t)H.n;
+    out->visited = inserted;
     if (rc != OR_OK) out->distance = rc;
     free(H.e); free(Hp.e); free(Q.a); free(Qp.a); free(q); og_free(&g);
     return rc;
+}
+
+int oracle_gwfa_ends(uint32_t nv, const char *seq, const uint64_t *seq_off,
+                     uint64_t na, const uint32_t *asrc, const uint32_t *adst,
+                     const char *qs, uint64_t n, uint32_t vs, uint32_t ve,
+                     int64_t a_diff, int64_t max_score, int ends, oracle_stats *out) {
+    return oracle_gwfa_ex(nv, seq, seq_off, na, asrc, adst, qs, n, vs, ve, a_diff, max_score, ends, 0, 0, out);
 }
 
 int oracle_gwfa(uint32_t nv, const char *seq, const uint64_t *seq_off,
