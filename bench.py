@@ -387,7 +387,7 @@ def main():
     h_order = pin(order.view(np.int32))
     h_out = torch.empty(len(qs) * gw.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
     lib = gw.load()
-    opts = gw.gwfa_opts(0, 0, -1, 0, 0)
+    opts = gw.gwfa_opts(0, 0, -1, 0, 0, 0, 0)
     import ctypes
 
     def e2e_step():

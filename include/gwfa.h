@@ -65,7 +65,15 @@ typedef struct {
                             v_e (Def. 2).  Needs max_lag == 0; the plain path and the
                             batch engine take it, the server and gwfa_align_noalloc
                             refuse it (GWFA_ERR_INVALID) */
-} gwfa_opts;                 /* 20 bytes */
+    int32_t evict_lag;   /* memory bound on H~ with pruning (max_lag > 0, no traceback): every
+                            evict_every scores, right after GwfExpand, the entries outside Q
+                            whose anti-diagonal i + W~ lags this score's maximum by evict_lag
+                            or more are removed; a removed diagonal may be inserted again
+                            (counted again in `visited`).  The distance stays an upper bound;
+                            the work counts change and `evicted` reports the removals.  0 = off;
+                            batch engine and plain path only */
+    int32_t evict_every; /* scores between two evictions; 0 = 64 */
+} gwfa_opts;                 /* 28 bytes */
 
 /* Formulation variants: the walk may begin at any position of v_s (its prefix is
  * skipped at no cost), may end at any position of v_e (its suffix skipped), or
@@ -98,7 +106,8 @@ typedef struct {
     uint32_t device_us;      /* device time the CTA spent on this query, microseconds */
     uint64_t pruned;
     uint64_t spills;
-} gwfa_result;               /* 56 bytes */
+    uint64_t evicted;        /* H~ entries removed by the memory bound (opts.evict_lag) */
+} gwfa_result;               /* 64 bytes */
 
 /* ---- graph -------------------------------------------------------------- */
 typedef struct gwfa_graph gwfa_graph;

@@ -28,12 +28,12 @@ GWFA_ERR_SCORE_LIMIT = -8
 GWFA_ERR_NOT_RUN = -9
 GWFA_MAX_TIERS = 4
 
-# numpy view of gwfa_result (56 bytes)
+# numpy view of gwfa_result (64 bytes)
 RESULT_DTYPE = np.dtype([("status", "<i4"), ("edit_distance", "<i4"), ("is_upper_bound", "<i4"),
                          ("n_scores", "<u4"), ("cells", "<u8"), ("visited", "<u8"),
                          ("peak_frontier", "<u4"), ("device_us", "<u4"), ("pruned", "<u8"),
-                         ("spills", "<u8")])
-assert RESULT_DTYPE.itemsize == 56
+                         ("spills", "<u8"), ("evicted", "<u8")])
+assert RESULT_DTYPE.itemsize == 64
 
 # numpy view of gwfa_cigar_result (16 bytes) and the CIGAR op codes (BAM's)
 CIGAR_RESULT_DTYPE = np.dtype([("status", "<i4"), ("cost", "<i4"), ("n_ops", "<u4"), ("walk_len", "<u4")])
@@ -43,7 +43,8 @@ CIGAR_CHARS = {GWFA_CIGAR_INS: "I", GWFA_CIGAR_DEL: "D", GWFA_CIGAR_EQ: "=", GWF
 
 class gwfa_opts(ctypes.Structure):
     _fields_ = [("max_lag", ctypes.c_int32), ("traceback", ctypes.c_int32),
-                ("max_score", ctypes.c_int32), ("wait_limit", ctypes.c_int32), ("ends", ctypes.c_int32)]
+                ("max_score", ctypes.c_int32), ("wait_limit", ctypes.c_int32), ("ends", ctypes.c_int32),
+                ("evict_lag", ctypes.c_int32), ("evict_every", ctypes.c_int32)]
 
 
 # formulation variants (gwfa_opts.ends flags)
@@ -55,7 +56,7 @@ class gwfa_result(ctypes.Structure):
                 ("is_upper_bound", ctypes.c_int32), ("n_scores", ctypes.c_uint32),
                 ("cells", ctypes.c_uint64), ("visited", ctypes.c_uint64),
                 ("peak_frontier", ctypes.c_uint32), ("device_us", ctypes.c_uint32),
-                ("pruned", ctypes.c_uint64), ("spills", ctypes.c_uint64)]
+                ("pruned", ctypes.c_uint64), ("spills", ctypes.c_uint64), ("evicted", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -204,8 +205,9 @@ def _c(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
-def _opts(max_lag: int, max_score: int, traceback: int = 0, ends: int = 0) -> gwfa_opts:
-    return gwfa_opts(int(max_lag), int(traceback), int(max_score), 0, int(ends))
+def _opts(max_lag: int, max_score: int, traceback: int = 0, ends: int = 0, evict_lag: int = 0,
+          evict_every: int = 0) -> gwfa_opts:
+    return gwfa_opts(int(max_lag), int(traceback), int(max_score), 0, int(ends), int(evict_lag), int(evict_every))
 
 
 class Graph:
@@ -234,10 +236,10 @@ class Graph:
         return {k: int(getattr(i, k)) for k, _ in i._fields_}
 
     def align(self, q: bytes, v_s: int, v_e: int, max_lag: int = 0, max_score: int = -1,
-              ends: int = 0) -> dict:
+              ends: int = 0, evict_lag: int = 0, evict_every: int = 0) -> dict:
         """Plain path (gwfa_align): one query, one kernel launch, synchronous."""
         r = gwfa_result()
-        o = _opts(max_lag, max_score, 0, ends)
+        o = _opts(max_lag, max_score, 0, ends, evict_lag, evict_every)
         qb = bytes(q)
         _check(load().gwfa_align(self.handle, qb, len(qb), v_s, v_e, ctypes.byref(o), ctypes.byref(r)),
                "gwfa_align")
@@ -311,7 +313,7 @@ class Engine:
 
     def align_batch(self, seq, off, v_s, v_e, order=None, max_lag: int = 0, max_score: int = -1,
                     stream: int = 0, out: np.ndarray | None = None, n_wide: int = 0,
-                    n_huge: int = 0, ends: int = 0) -> np.ndarray:
+                    n_huge: int = 0, ends: int = 0, evict_lag: int = 0, evict_every: int = 0) -> np.ndarray:
         """Host buffers in, host results out (gwfa_align_batch)."""
         seq = _c(seq, np.uint8)
         off = _c(off, np.uint64)
@@ -319,7 +321,7 @@ class Engine:
         ve = _c(v_e, np.uint32)
         n = len(vs)
         res = out if out is not None else np.zeros(n, dtype=RESULT_DTYPE)
-        o = _opts(max_lag, max_score, 0, ends)
+        o = _opts(max_lag, max_score, 0, ends, evict_lag, evict_every)
         od = None if order is None else _c(order, np.uint32)
         _check(load().gwfa_align_batch(self.handle, n, seq.ctypes.data, off.ctypes.data, vs.ctypes.data,
                                        ve.ctypes.data, None if od is None else od.ctypes.data,
@@ -331,9 +333,10 @@ class Engine:
     def align_batch_device(self, n: int, d_words: int, d_q_off: int, d_v_s: int, d_v_e: int,
                            d_order: int | None, d_status: int | None, d_out: int,
                            max_lag: int = 0, max_score: int = -1, stream: int = 0, n_wide: int = 0,
-                           traceback: bool = False, n_huge: int = 0, ends: int = 0):
+                           traceback: bool = False, n_huge: int = 0, ends: int = 0, evict_lag: int = 0,
+                           evict_every: int = 0):
         """Device pointers in and out, asynchronous on `stream` (gwfa_align_batch_device)."""
-        o = _opts(max_lag, max_score, int(traceback), ends)
+        o = _opts(max_lag, max_score, int(traceback), ends, evict_lag, evict_every)
         _check(load().gwfa_align_batch_device(self.handle, n, d_words, d_q_off, d_v_s, d_v_e,
                                               d_order or None, _sched(n_huge, n_wide), d_status or None,
                                               ctypes.byref(o),
@@ -385,14 +388,15 @@ class DeviceBatch:
                             self.status.data_ptr(), st.cuda_stream)
 
     def run(self, engine: Engine, max_lag: int = 0, max_score: int = -1, stream=None, n_wide: int = 0,
-            traceback: bool = False, n_huge: int = 0, ends: int = 0):
+            traceback: bool = False, n_huge: int = 0, ends: int = 0, evict_lag: int = 0,
+            evict_every: int = 0):
         import torch
         st = stream if stream is not None else torch.cuda.current_stream(self.q.device)
         engine.align_batch_device(self.n, self.words.data_ptr(), self.q_off.data_ptr(),
                                   self.v_s.data_ptr(), self.v_e.data_ptr(),
                                   None if self.order is None else self.order.data_ptr(),
                                   self.status.data_ptr(), self.out.data_ptr(), max_lag, max_score,
-                                  st.cuda_stream, n_wide, traceback, n_huge, ends)
+                                  st.cuda_stream, n_wide, traceback, n_huge, ends, evict_lag, evict_every)
 
     def results(self) -> np.ndarray:
         return self.out.cpu().numpy().view(RESULT_DTYPE)

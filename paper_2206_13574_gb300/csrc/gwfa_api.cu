@@ -217,9 +217,11 @@ static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_
                        const gwfa_opts &o, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
                        uint32_t *path_len);
 
-// formulation variant flags: known bits only, and not combined with pruning
+// formulation variant flags: known bits only, and not combined with pruning; the
+// memory bound on H~ needs pruning and the walk base in the payload (no traceback)
 static bool ends_ok(const gwfa_opts &o) {
-    return (o.ends & ~(GWFA_FREE_START | GWFA_FREE_END | GWFA_EXTEND)) == 0 && (o.ends == 0 || o.max_lag == 0);
+    return (o.ends & ~(GWFA_FREE_START | GWFA_FREE_END | GWFA_EXTEND)) == 0 && (o.ends == 0 || o.max_lag == 0) &&
+           o.evict_lag >= 0 && o.evict_every >= 0 && (o.evict_lag == 0 || (o.max_lag > 0 && !o.traceback));
 }
 
 int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
@@ -318,6 +320,8 @@ static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_
         a.max_score = o.max_score;
         a.traceback = o.traceback ? 1 : 0;
         a.ends = o.ends;
+        a.evict_lag = o.evict_lag;
+        a.evict_every = o.evict_every ? o.evict_every : 64;
         a.paths = o.traceback ? d_path : nullptr;
         a.path_len = o.traceback ? d_plen : nullptr;
         a.path_cap = path_cap;
@@ -547,6 +551,8 @@ static TierArgs tier_args(gwfa_engine *e, const uint32_t *d_words, const uint64_
     a.stats = e->stats;
     a.traceback = o.traceback ? 1 : 0;
     a.ends = o.ends;
+    a.evict_lag = o.evict_lag;
+    a.evict_every = o.evict_every ? o.evict_every : 64;
     a.paths = e->paths;
     a.path_len = e->path_len;
     a.path_cap = e->path_cap;

@@ -110,6 +110,8 @@ struct TierArgs {
     int q_smem;                 // query words are in shared memory (server kernel)
     int traceback;              // 64-bit values carry a trace index (Alg. 5-6) instead of a base
     int ends;                   // formulation variant flags (GWFA_FREE_START / _FREE_END / _EXTEND)
+    int evict_lag;              // memory bound on H~ (pruning mode): lag behind a_max, 0 = off
+    int evict_every;            // scores between two evictions
     uint32_t *paths;            // traceback: path_cap vertex ids per query id
     uint32_t *path_len;         // traceback: walk length per query id (may exceed path_cap)
     uint32_t path_cap;

@@ -100,7 +100,8 @@ struct Sh {
     uint32_t nt;        // tiles claimed (touched) this query
     uint32_t score_cells;
     unsigned long long amax;
-    unsigned long long cells, visited, pruned, spills;
+    unsigned long long cells, visited, pruned, spills, evicted;
+    uint32_t nsurv;     // memory bound: tiles kept by the last eviction
     uint32_t peak;
     uint32_t claim[3];  // work counters of the phases, rotating (see align_one)
     uint32_t tlen;      // traceback: entries of T
@@ -600,6 +601,68 @@ __device__ void wipe_touched(const Slab<P> &s, uint32_t nt) {
     }
 }
 
+// Memory bound on H~ (pruning mode, called every evict_every scores right after
+// GwfExpand): the lanes in the new Q (registered in parity `par`) and those whose
+// anti-diagonal a = i + W~ lags this score's a_max by less than `lag` are kept, the
+// others are removed (sh.evicted).  The tiles with a kept lane are staged in the
+// frontier-snapshot list, which is free between scores; the table is wiped through
+// the touched list and they are inserted again, and Q is rebuilt with their new
+// slots.  A removed diagonal may be inserted again later, like any absent one.
+__device__ void evict_behind(const Slab<true> &s, Sh &sh, long long amax, int lag, int par,
+                             uint32_t *qcount) {
+    const uint32_t nt = min(sh.nt, s.cap);
+    if (threadIdx.x == 0) sh.nsurv = 0;
+    __syncthreads();
+    unsigned long long ev = 0;
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) {
+        const uint32_t slot = __ldcg(&s.touched[t]);
+        const unsigned long long key = __ldcg(&s.slots[slot].key);
+        const uint32_t regw = __ldcg(&s.slots[slot].reg[par]);
+        const int kb = (int)(uint32_t)(key & 0xFFFFFFFFull);
+        long long v8[kTile];
+        uint32_t keep = 0;
+#pragma unroll
+        for (int ln = 0; ln < kTile; ++ln) {
+            v8[ln] = __ldcg(&s.slots[slot].vals[ln]);
+            if (v8[ln] < 0) continue;
+            const int j = pj(v8[ln]);
+            const long long a = (long long)(kb * kTile + ln) + 2ll * j + (long long)pbase(v8[ln]);
+            if (((regw >> ln) & 1u) || amax - a < (long long)lag) keep |= 1u << ln;
+            else ++ev;
+        }
+        if (keep) {
+            const uint32_t i = atomicAdd(&sh.nsurv, 1u);   // i < nt <= cap
+            st_ehdr(&s.elist[i].hdr, regw, (uint32_t)(key >> 32), kb, 0u);
+#pragma unroll
+            for (int ln = 0; ln < kTile; ++ln)
+                __stcg(&s.elist[i].vals[ln], ((keep >> ln) & 1u) ? v8[ln] : -1ll);
+        }
+    }
+    if (ev) atomicAdd(&sh.evicted, ev);
+    __syncthreads();
+    wipe_touched<true>(s, nt);
+    if (threadIdx.x == 0) {
+        sh.nt = 0;
+        *qcount = 0;
+    }
+    __syncthreads();
+    const uint32_t ns = sh.nsurv;
+    for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        const EHdr h = ld_ehdr(&s.elist[i].hdr);
+        const int slot = find_or_insert(s, sh, tile_key(h.v, h.kb));
+        if (slot < 0) continue;
+#pragma unroll
+        for (int ln = 0; ln < kTile; ++ln) __stcg(&s.slots[slot].vals[ln], __ldcg(&s.elist[i].vals[ln]));
+        if (h.slot_mask) {   // part of the new Q
+            __stcg(&s.slots[slot].reg[par], h.slot_mask);
+            const uint32_t qi = atomicAdd(qcount, 1u);
+            if (qi < s.cap) __stcg((uint4 *)&s.qlist[qi], make_uint4((uint32_t)slot, h.v, (uint32_t)h.kb, 0u));
+            else set_err(sh, GWFA_ERR_CAPACITY);
+        }
+    }
+    __syncthreads();
+}
+
 template <bool P>
 __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t qid) {
     const DevGraph &g = A.g;
@@ -633,7 +696,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
     if (threadIdx.x == 0) {
         sh.err = 0;
         sh.nt = 0;
-        sh.cells = sh.visited = sh.pruned = sh.spills = 0;
+        sh.cells = sh.visited = sh.pruned = sh.spills = sh.evicted = 0;
         sh.peak = 0;
         sh.nq[0] = sh.nq[1] = 0;
         sh.claim[0] = sh.claim[1] = sh.claim[2] = 0;
@@ -770,6 +833,13 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             status = P && A.max_lag > 0 ? GWFA_ERR_EMPTY_FRONTIER : GWFA_ERR_UNREACHABLE;
             break;
         }
+        if constexpr (P) {
+            if (A.evict_lag > 0 && d % A.evict_every == 0) {
+                evict_behind(s, sh, amax, A.evict_lag, phase & 1, &sh.nq[d & 1]);
+                failed = __syncthreads_or(sh.err != 0);
+                if (failed) break;
+            }
+        }
     }
     __syncthreads();
     if (failed) status = sh.err;   // stable now: every thread has left the processing phases
@@ -789,6 +859,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             r.peak_frontier = sh.peak;
             r.pruned = sh.pruned;
             r.spills = sh.spills;
+            r.evicted = sh.evicted;
             if constexpr (P) {
                 if (A.traceback && status == 0) {
                     // GwfTraceback (Alg. 6): push the end vertex, then follow T back to the

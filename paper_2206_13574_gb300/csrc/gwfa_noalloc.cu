@@ -59,7 +59,7 @@ extern "C" int gwfa_align_noalloc(const gwfa_graph *g, uint32_t n_queries, const
                                   gwfa_result *d_out, void *stream) {
     if (!g || !d_words || !d_q_off || !d_v_s || !d_v_e || !d_out) return GWFA_ERR_INVALID;
     const gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || o.traceback != 0 || o.ends != 0) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || o.traceback != 0 || o.ends != 0 || o.evict_lag != 0) return GWFA_ERR_INVALID;
     if (log2_tiles == 0) log2_tiles = 15;
     const bool prune = o.max_lag > 0;
     if (log2_tiles < 8 || log2_tiles > gwfa::kMaxLog2Tiles) return GWFA_ERR_CAPACITY;

@@ -168,7 +168,7 @@ int gwfa_server_create(const gwfa_graph *g, const gwfa_server_config *cfg, const
         (c.ctas_big && (c.log2_big < 8 || c.log2_big > gwfa::kMaxLog2Tiles)))
         return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || o.traceback != 0 || o.ends != 0) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || o.traceback != 0 || o.ends != 0 || o.evict_lag != 0) return GWFA_ERR_INVALID;
     int st = sstat(cudaSetDevice(g->device));
     if (st) return st;
     gwfa_server *sv = new (std::nothrow) gwfa_server();

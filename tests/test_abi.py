@@ -28,9 +28,9 @@ def test_library_builds_and_exports_header_symbols():
 
 
 def test_struct_layouts_match_header():
-    assert ctypes.sizeof(gw.gwfa_result) == 56
-    assert gw.RESULT_DTYPE.itemsize == 56
-    assert ctypes.sizeof(gw.gwfa_opts) == 20
+    assert ctypes.sizeof(gw.gwfa_result) == 64
+    assert gw.RESULT_DTYPE.itemsize == 64
+    assert ctypes.sizeof(gw.gwfa_opts) == 28
     assert ctypes.sizeof(gw.gwfa_engine_config) == 128   # 108 bytes of u32 fields, padded to 8
     assert ctypes.sizeof(gw.gwfa_schedule) == 8
     assert gw.CIGAR_RESULT_DTYPE.itemsize == 16

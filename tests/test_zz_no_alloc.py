@@ -26,7 +26,7 @@ def test_noalloc_matches_engine_twice(max_lag):
                                                           max_lag=max_lag)
     batch = gw.DeviceBatch(sub)
     lib = gw.load()
-    opts = gw.gwfa_opts(max_lag, 0, -1, 0, 0)
+    opts = gw.gwfa_opts(max_lag, 0, -1, 0, 0, 0, 0)
     for call in range(2):
         batch.out.fill_(0xAB)
         st = lib.gwfa_align_noalloc(graph.handle, batch.n, batch.words.data_ptr(), batch.q_off.data_ptr(),
