@@ -57,6 +57,26 @@ def config3(n_pruned: int = 2000, n_exact: int = 200, a_diff: int = 1000) -> dic
     ex = be.results()
     enge.close()
     torch.cuda.synchronize()
+    # the same pruned run with H~ bounded to the lag window, on slabs 16x smaller
+    cfgb = gw.default_config(graph, prune=True)
+    slab_small = cfgb.tiers[0].log2_tiles - 4
+    cfgb.tiers[0].log2_tiles = slab_small
+    engb = gw.Engine(graph, prune=True, config=cfgb)
+    bp.run(engb, max_lag=a_diff, evict_lag=a_diff, evict_every=64)
+    t_b = _timed_run(engb, bp, max_lag=a_diff, evict_lag=a_diff, evict_every=64)
+    bd = bp.results()
+    bounded = {"slab_log2_tiles": slab_small, "evict_lag": a_diff, "evict_every": 64, "s": t_b,
+               "gbp_per_s": float(qs.lengths()[bd["status"] == 0].sum()) / t_b / 1e9,
+               "engine_bytes": engb.device_bytes, "tier0_overflows": int(engb.last_retries()[0]),
+               "evicted": int(bd["evicted"].sum()), "cells": int(bd["cells"].sum()),
+               "ok": int((bd["status"] == 0).sum())}
+    engb.close()
+    free_retries = None
+    engp2 = gw.Engine(graph, prune=True)
+    bp.run(engp2, max_lag=a_diff)
+    free_retries = int(engp2.last_retries()[0])
+    free_bytes = engp2.device_bytes
+    engp2.close()
     prs = pr[:n_exact]
     ok = (ex["status"] == 0) & (prs["status"] == 0)
     return {"workload": "config3: 1 Mb cyclic graph (tandem-repeat loops), 50 kb queries, 8% errors",
@@ -68,6 +88,10 @@ def config3(n_pruned: int = 2000, n_exact: int = 200, a_diff: int = 1000) -> dic
                       "gbp_per_s": float(sub.lengths()[ex["status"] == 0].sum()) / t_ex / 1e9,
                       "cells": int(ex["cells"].sum()), "ok": int((ex["status"] == 0).sum()),
                       "mean_distance": float(ex["edit_distance"][ex["status"] == 0].mean())},
+            "bounded_memory": dict(bounded, unbounded_engine_bytes=free_bytes,
+                                   unbounded_tier0_overflows=free_retries,
+                                   exact_match_rate=float((bd["edit_distance"][:n_exact][ok] ==
+                                                           ex["edit_distance"][ok]).mean())),
             "exact_match_rate": float((prs["edit_distance"][ok] == ex["edit_distance"][ok]).mean()),
             "pruned_never_below_exact": bool(np.all(prs["edit_distance"][ok] >= ex["edit_distance"][ok])),
             "work_ratio_exact_over_pruned": float(ex["cells"][ok].sum() / max(prs["cells"][ok].sum(), 1))}
