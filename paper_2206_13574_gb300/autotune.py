@@ -1,7 +1,7 @@
 """Launch-shape autotuner for the batched engine.
 
-Grid search on a held-out sample of queries over the CTA width (8-lane groups
-per query: threads / 8), CTAs per SM and tier-0 slab size; every candidate must
+Grid search on a held-out sample of queries over the CTA width (2 to 16 warps per
+query, i.e. 8 to 64 8-lane groups: threads / 8), CTAs per SM and tier-0 slab size; every candidate must
 give the same results (they are compared), the fastest is kept.  Results are
 persisted as JSON keyed by (graph fingerprint, GPU name, mode), so later runs on
 the same graph and GPU reuse them without searching again.
@@ -46,7 +46,7 @@ def _time(engine: Engine, batch: DeviceBatch, max_lag: int, reps: int) -> float:
     return best
 
 
-def autotune(graph: Graph, sample, max_lag: int = 0, threads=(256, 512), per_sm_frac=(0.5, 1.0),
+def autotune(graph: Graph, sample, max_lag: int = 0, threads=(64, 128, 256, 512), per_sm_frac=(0.5, 1.0),
              log2_tiles=(15, 16), reps: int = 2, cache_path: str | None = DEFAULT_CACHE,
              force: bool = False) -> dict:
     """Best {threads, ctas, log2_tiles} for `graph` from a timing sweep on `sample`."""

@@ -112,17 +112,35 @@ def predicted_time(pred: np.ndarray, coeffs: tuple[float, float] | None) -> np.n
     return coeffs[0] * (d + 1.0) + coeffs[1] * cells
 
 
+def lpt_max_load(times: np.ndarray, ctas: int) -> float:
+    """Largest CTA load when `times` are handed out longest first to `ctas` CTAs, each
+    taking the next one when it becomes free (the work queue's behaviour)."""
+    import heapq
+    loads = [0.0] * max(ctas, 1)
+    for x in sorted((float(v) for v in times), reverse=True):
+        heapq.heappush(loads, heapq.heappop(loads) + x)
+    return max(loads)
+
+
 def wide_ctas(pred: np.ndarray, order: np.ndarray, n_wide: int, total_ctas: int,
               coeffs: tuple[float, float] | None = None, first: int = 0) -> int:
     """CTAs for a large-slab class holding queue positions [first, first + n_wide):
     its share of the predicted CTA time (or of the predicted cells without time
-    coefficients) times the CTAs that fit on the GPU, at least one, at most one per
-    query of the class."""
+    coefficients) times the CTAs that fit on the GPU -- raised until the class's own
+    longest-first packing ends within the batch's predicted time (the larger of the
+    total time spread over every CTA and the longest single query), because a class
+    with too few CTAs turns its heaviest queries into a tail; at least one, at most
+    one per query of the class."""
     if n_wide == 0:
         return 0
     t = predicted_time(pred, coeffs)
-    share = t[order[first:first + n_wide]].sum() / max(t.sum(), 1e-9)
-    return int(min(n_wide, max(1, round(total_ctas * share))))
+    tw = t[order[first:first + n_wide]]
+    share = tw.sum() / max(t.sum(), 1e-9)
+    c = int(min(n_wide, max(1, round(total_ctas * share))))
+    bound = max(t.sum() / max(total_ctas, 1), float(tw.max())) * 1.05
+    while c < n_wide and lpt_max_load(tw, c) > bound:
+        c = min(n_wide, c + max(1, c // 8))
+    return c
 
 
 def spearman(a: np.ndarray, b: np.ndarray) -> float:
@@ -132,4 +150,4 @@ def spearman(a: np.ndarray, b: np.ndarray) -> float:
 
 
 __all__ = ["collect", "fit", "plan", "r2", "save", "load_into", "transfer", "targets_of", "spearman",
-           "time_coeffs", "predicted_time", "wide_ctas", "capacities", "MODEL_TARGETS", "Graph"]
+           "time_coeffs", "predicted_time", "wide_ctas", "lpt_max_load", "capacities", "MODEL_TARGETS", "Graph"]

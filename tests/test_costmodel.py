@@ -174,3 +174,30 @@ def test_learned_schedule_keeps_results_and_avoids_overflow_reruns(c2small):
         assert np.array_equal(plain[f], learned[f]), f
     assert plain_retries > 0
     assert learned_retries < plain_retries, (learned_retries, plain_retries, n_wide)
+
+
+def test_lpt_packing_and_wide_class_sizing():
+    """Host side of the plan: longest-first packing onto a work queue, and a large-slab
+    class that gets one CTA per heavy query when those queries are the critical path."""
+    from paper_2206_13574_gb300 import costmodel as cm
+    assert cm.lpt_max_load([5, 4, 3, 3, 2], 2) == 9
+    assert cm.lpt_max_load([1] * 10, 5) == 2
+    assert cm.lpt_max_load([7], 3) == 7
+
+    def pred_of(times):
+        p = np.zeros((len(times), 4), np.float32)
+        p[:, 0] = -1e-3                 # predicted distance ~0: time ~ cells without coefficients
+        p[:, 3] = np.log1p(times)
+        return p
+
+    # 24 queries each as long as the whole batch would take: one CTA each
+    t = np.concatenate([np.full(24, 100.0), np.ones(10000)])
+    p = pred_of(t)
+    order = np.argsort(-t, kind="stable")
+    assert cm.wide_ctas(p, order, 24, 608) == 24
+    # heavy but short next to the batch: the time share is enough
+    t = np.concatenate([np.full(200, 5.0), np.ones(100000)])
+    p = pred_of(t)
+    order = np.argsort(-t, kind="stable")
+    c = cm.wide_ctas(p, order, 200, 608)
+    assert c < 200 and c >= round(608 * 1000 / 101000)
