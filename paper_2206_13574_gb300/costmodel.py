@@ -129,10 +129,14 @@ def wide_ctas(pred: np.ndarray, order: np.ndarray, n_wide: int, total_ctas: int,
     coefficients) times the CTAs that fit on the GPU -- raised until the class's own
     longest-first packing ends within the batch's predicted time (the larger of the
     total time spread over every CTA and the longest single query), because a class
-    with too few CTAs turns its heaviest queries into a tail; at least one, at most
-    one per query of the class."""
+    with too few CTAs turns its heaviest queries into a tail; one per query when the
+    class is small; at least one, at most one per query of the class."""
     if n_wide == 0:
         return 0
+    if n_wide * 8 <= total_ctas:
+        # a few heavy queries: one CTA each costs at most an eighth of the GPU for the
+        # time the lighter ones keep it busy, and no heavy query waits for another
+        return int(n_wide)
     t = predicted_time(pred, coeffs)
     tw = t[order[first:first + n_wide]]
     share = tw.sum() / max(t.sum(), 1e-9)
