@@ -241,6 +241,25 @@ def test_edge_cases():
     assert r["status"] == gw.GWFA_ERR_SCORE_LIMIT
 
 
+def test_longest_queries_and_empty_batch():
+    """100 kb queries (the longest of the lognormal workloads) against the oracle, on
+    the batch and plain paths; an empty batch is a no-op."""
+    c = synth.CONFIGS[4]
+    g = synth.make_graph(synth.dataclasses.replace(c["graph"], backbone=400_000), 4)
+    qs = synth.make_queries(g, 4, 41, synth._const(100_000), synth._const(0.004), c["weights"], c["loops"])
+    graph = gw.Graph.from_synth(g)
+    eng = gw.Engine(graph)
+    res = eng.align_batch(qs.seq, qs.off, qs.v_s, qs.v_e)
+    want = oracle.gwfa_many(g, qs, range(len(qs)))
+    for i, w in enumerate(want):
+        assert qs.lengths()[i] >= 100_000
+        assert_same(res[i], w, f"long{i}")
+    assert_same(graph.align(qs.query(0), int(qs.v_s[0]), int(qs.v_e[0])), want[0], "plain long0")
+    empty = eng.align_batch(np.zeros(0, np.uint8), np.zeros(1, np.uint64), np.zeros(0, np.uint32),
+                            np.zeros(0, np.uint32))
+    assert len(empty) == 0
+
+
 def test_device_batch_replays_as_cuda_graph():
     """The device-resident batch call (counter reset + tier launches, no host sync) is
     captured once into a CUDA graph and replayed; results match the direct call."""
