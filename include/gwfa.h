@@ -311,9 +311,13 @@ int gwfa_engine_last_retries(gwfa_engine *e, uint32_t *out);
  * alignment; the paper's discussion (Sec. 4) obtains one by aligning the query
  * to the sequence the walk spells with a pairwise method.  This step does that on
  * the device: for each query it spells sigma(w) (2-bit packed) and runs a
- * pairwise edit-distance wavefront alignment (unit costs, both ends global)
- * bounded by the query's reported distance, then walks the stored wavefronts
- * back to a CIGAR.  When w is optimal the CIGAR has exactly edit_distance edits.
+ * pairwise edit-distance wavefront alignment (unit costs) bounded by the query's
+ * reported distance, then walks the stored wavefronts back to a CIGAR.  The ends
+ * follow the batch's formulation (`ends`, GWFA_FREE_* / GWFA_EXTEND): the query is
+ * always aligned whole; the walk's first vertex may be entered past its start
+ * under GWFA_FREE_START, its last vertex left before its end under GWFA_FREE_END
+ * or GWFA_EXTEND; [walk_begin, walk_end) is the aligned part of sigma(w).  When w
+ * is optimal the CIGAR has exactly edit_distance edits.
  *
  * CIGAR operations are uint32 (length << 4 | op) with the BAM op codes below,
  * query = the read, walk = the reference: '=' a run of equal bases, 'X' one
@@ -334,13 +338,15 @@ typedef struct {
     int32_t cost;         /* edits of the CIGAR */
     uint32_t n_ops;       /* CIGAR operations */
     uint32_t walk_len;    /* bases spelled by the walk */
-} gwfa_cigar_result;      /* 16 bytes */
+    uint32_t walk_begin;  /* first aligned base of sigma(w) (0 unless GWFA_FREE_START) */
+    uint32_t walk_end;    /* one past the last aligned base (walk_len unless a free end) */
+} gwfa_cigar_result;      /* 24 bytes */
 
 /*
  * ctas: persistent CTAs (0 = 2 per SM); workspace_bytes: device scratch per CTA
- * (0 = 8 MiB).  A query needs 4 * (|sigma(w)| / 16 + 2) + 4 * (d + 1)^2 bytes
- * (rounded up to 16) of it: the default holds distances up to ~1400 for walks of
- * tens of kb.  The workspace is allocated here; gwfa_cigar_device allocates
+ * (0 = 8 MiB).  A query needs 4 * (|sigma(w)| / 16 + 2) + 4 * (d + 1) * (d + 1 + L)
+ * bytes (the first term rounded up to 16; L = |first vertex| under GWFA_FREE_START,
+ * else 0) of it: the default holds distances up to ~1400 for walks of tens of kb.  The workspace is allocated here; gwfa_cigar_device allocates
  * nothing.
  */
 int gwfa_cigar_create(const gwfa_graph *g, uint32_t ctas, uint64_t workspace_bytes, gwfa_cigar **out);
@@ -354,15 +360,13 @@ int gwfa_cigar_destroy(gwfa_cigar *c);
  *   d_cigar           n_queries * cigar_cap operations; query i writes from
  *                     d_cigar[i * cigar_cap]
  *   d_out             n_queries results
- * Calls on one gwfa_cigar share its workspace: order them on one stream.  The
- * alignment is global over the whole spelled walk, so it is meant for batches
- * aligned with ends = 0 (a walk of a free-end variant may cost more than d
- * globally: GWFA_ERR_SCORE_LIMIT).
+ *   ends              the formulation flags the batch was aligned with
+ * Calls on one gwfa_cigar share its workspace: order them on one stream.
  */
 int gwfa_cigar_device(gwfa_cigar *c, uint32_t n_queries, const uint32_t *d_words,
                       const uint64_t *d_q_off, const gwfa_result *d_res, const uint32_t *d_paths,
                       uint32_t path_cap, const uint32_t *d_path_len, uint32_t *d_cigar,
-                      uint32_t cigar_cap, gwfa_cigar_result *d_out, void *stream);
+                      uint32_t cigar_cap, int32_t ends, gwfa_cigar_result *d_out, void *stream);
 
 /* ---- learned cost model (scheduling only; never changes a result) -------- */
 /*

@@ -35,8 +35,9 @@ RESULT_DTYPE = np.dtype([("status", "<i4"), ("edit_distance", "<i4"), ("is_upper
                          ("spills", "<u8"), ("evicted", "<u8")])
 assert RESULT_DTYPE.itemsize == 64
 
-# numpy view of gwfa_cigar_result (16 bytes) and the CIGAR op codes (BAM's)
-CIGAR_RESULT_DTYPE = np.dtype([("status", "<i4"), ("cost", "<i4"), ("n_ops", "<u4"), ("walk_len", "<u4")])
+# numpy view of gwfa_cigar_result (24 bytes) and the CIGAR op codes (BAM's)
+CIGAR_RESULT_DTYPE = np.dtype([("status", "<i4"), ("cost", "<i4"), ("n_ops", "<u4"), ("walk_len", "<u4"),
+                               ("walk_begin", "<u4"), ("walk_end", "<u4")])
 GWFA_CIGAR_INS, GWFA_CIGAR_DEL, GWFA_CIGAR_EQ, GWFA_CIGAR_DIFF = 1, 2, 7, 8
 CIGAR_CHARS = {GWFA_CIGAR_INS: "I", GWFA_CIGAR_DEL: "D", GWFA_CIGAR_EQ: "=", GWFA_CIGAR_DIFF: "X"}
 
@@ -126,7 +127,7 @@ SIGNATURES.update({
     "gwfa_plan_schedule": ([_u32, _P, _u64, _u64, _P, _P], ctypes.c_int),
     "gwfa_cigar_create": ([_P, _u32, _u64, ctypes.POINTER(_P)], ctypes.c_int),
     "gwfa_cigar_destroy": ([_P], ctypes.c_int),
-    "gwfa_cigar_device": ([_P, _u32, _P, _P, _P, _P, _u32, _P, _P, _u32, _P, _P], ctypes.c_int),
+    "gwfa_cigar_device": ([_P, _u32, _P, _P, _P, _P, _u32, _P, _P, _u32, _i32, _P, _P], ctypes.c_int),
 })
 
 
@@ -502,13 +503,14 @@ class Cigar:
         self.handle = h
 
     def run_device(self, n: int, d_words: int, d_q_off: int, d_res: int, d_paths: int, path_cap: int,
-                   d_path_len: int, d_cigar: int | None, cigar_cap: int, d_out: int, stream: int = 0):
+                   d_path_len: int, d_cigar: int | None, cigar_cap: int, d_out: int, stream: int = 0,
+                   ends: int = 0):
         _check(load().gwfa_cigar_device(self.handle, n, d_words, d_q_off, d_res, d_paths, path_cap,
-                                        d_path_len, d_cigar or None, cigar_cap, d_out, stream or None),
+                                        d_path_len, d_cigar or None, cigar_cap, int(ends), d_out, stream or None),
                "gwfa_cigar_device")
 
     def run(self, batch: "DeviceBatch", paths, path_len, path_cap: int, cigar_cap: int = 1024,
-            stream=None):
+            stream=None, ends: int = 0):
         """CIGARs of a batch after a traceback run whose walks are in the device
         tensors `paths` / `path_len`; returns (ops tensor n x cigar_cap, results tensor)."""
         import torch
@@ -518,7 +520,7 @@ class Cigar:
         st = stream if stream is not None else torch.cuda.current_stream(dev)
         self.run_device(batch.n, batch.words.data_ptr(), batch.q_off.data_ptr(), batch.out.data_ptr(),
                         paths.data_ptr(), path_cap, path_len.data_ptr(), ops.data_ptr(), cigar_cap,
-                        out.data_ptr(), st.cuda_stream)
+                        out.data_ptr(), st.cuda_stream, ends)
         return ops, out
 
     def close(self):

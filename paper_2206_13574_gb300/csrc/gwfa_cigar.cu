@@ -11,14 +11,18 @@
 //      (i in the query, j in the walk) at score s from score s - 1 (substitution
 //      i+1, j+1; query base skipped i+1; walk base skipped j+1), extend it along
 //      equal bases 16 at a time (XOR of packed windows, first set bit), and keep
-//      every wavefront: score s occupies s^2 .. s^2 + 2s of the array;
-//   3. once the end point (n, m) is on a wavefront, one thread walks the stored
+//      every wavefront.  Score 0 starts at (0, 0), or at every (0, j) of the first
+//      vertex when the walk may start inside it (L = its length, else L = 0), so
+//      score s spans diagonals -s .. L + s and starts at offset s (L + s);
+//   3. once an end point is on a wavefront -- (n, m), or (n, j) for any j in the
+//      last vertex when the walk may end inside it -- one thread walks the stored
 //      wavefronts back: each step re-derives which predecessor gave the point's
 //      starting offset, emitting the run of equal bases and one edit.
 //
 // The score loop is bounded by the query's Gwfa distance d: when w is optimal,
-// the pairwise distance of q and sigma(w) is d (an alignment of q to a walk is
-// an alignment to its spelled sequence and back), so (d+1)^2 offsets suffice.
+// the pairwise distance of q and sigma(w) (with the same free ends) is d (an
+// alignment of q to a walk is an alignment to its spelled sequence and back), so
+// (d + 1) (d + 1 + L) offsets suffice.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -49,6 +53,7 @@ struct CigarArgs {
     uint32_t *cigar;
     uint32_t cigar_cap;
     gwfa_cigar_result *out;
+    int ends;
     uint8_t *ws;
     uint64_t ws_bytes;
     uint32_t n;
@@ -82,27 +87,33 @@ __device__ int run_length(const uint32_t *qw, int i, const uint32_t *tw, int j, 
 }
 
 // The three predecessors of diagonal k at score s (prev = wavefront s - 1, indexed
-// by diagonal): the query offset each would start k at, or -1 where the move is
-// impossible (unreached predecessor, or it would leave the n x m rectangle).
+// by diagonal, spanning lo .. hi): the query offset each would start k at, or -1
+// where the move is impossible (unreached predecessor, or it would leave the
+// n x m rectangle).
 struct Pred {
     int sub, ins, del;
 };
-__device__ __forceinline__ Pred predecessors(const int *prev, int s, int k, int n, int m) {
+__device__ __forceinline__ Pred predecessors(const int *prev, int lo, int hi, int k, int n, int m) {
     Pred p{-1, -1, -1};
-    const int r = s - 1;   // wavefront s - 1 spans diagonals -r .. r
-    if (k >= -r && k <= r) {
+    if (k >= lo && k <= hi) {
         const int v = __ldcg(prev + k);
         if (v >= 0 && v < n && v + k < m) p.sub = v + 1;        // (v, v+k) -> (v+1, v+k+1)
     }
-    if (k + 1 <= r) {
+    if (k + 1 >= lo && k + 1 <= hi) {
         const int v = __ldcg(prev + k + 1);
         if (v >= 0 && v < n) p.ins = v + 1;                     // (v, v+k+1) -> (v+1, v+k+1)
     }
-    if (k - 1 >= -r) {
+    if (k - 1 >= lo && k - 1 <= hi) {
         const int v = __ldcg(prev + k - 1);
         if (v >= 0 && v + k - 1 < m) p.del = v;                 // (v, v+k-1) -> (v, v+k)
     }
     return p;
+}
+
+// wavefront s of a run whose score 0 spans diagonals 0 .. L: diagonals -s .. L + s,
+// stored from offset s (L + s), indexed by diagonal
+__device__ __forceinline__ int *wavefront(int *wf, int s, int L) {
+    return wf + (int64_t)s * (L + s) + s;
 }
 
 struct Runs {
@@ -128,11 +139,11 @@ struct Runs {
 };
 
 __device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsigned long long &s_sum,
-                           uint32_t *s_warp, uint32_t &s_base) {
+                           uint32_t *s_warp, uint32_t &s_base, int &s_hitk) {
     const int tid = threadIdx.x;
     const gwfa_result r = A.res[qid];
     const uint32_t plen = A.path_len[qid];
-    gwfa_cigar_result o = {GWFA_OK, 0, 0, 0};
+    gwfa_cigar_result o = {GWFA_OK, 0, 0, 0, 0, 0};
     if (r.status != GWFA_OK || plen == 0) o.status = GWFA_ERR_NOT_RUN;
     else if (plen > A.path_cap) o.status = GWFA_ERR_CAPACITY;
     if (o.status) {   // uniform: every thread read the same words
@@ -154,9 +165,14 @@ __device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsig
     const unsigned long long m64 = s_sum;
     const int n = (int)(A.q_off[qid + 1] - A.q_off[qid]);
     const int d = r.edit_distance;
+    // free ends: lengths of the first and last vertices (0 = the end is fixed)
+    const uint32_t v_first = __ldg(walk), v_last = __ldg(walk + plen - 1);
+    const int L = (A.ends & GWFA_FREE_START) && v_first < A.g.nv ? (int)__ldg(&A.g.vinfo[v_first]).y : 0;
+    const bool free_end = (A.ends & (GWFA_FREE_END | GWFA_EXTEND)) != 0;
+    const int l_last = free_end && v_last < A.g.nv ? (int)__ldg(&A.g.vinfo[v_last]).y : 0;
     const uint64_t t_words = (m64 >> 4) + 2;
     const uint64_t wf_off = (t_words * 4 + 15) & ~15ull;
-    const uint64_t need = wf_off + (uint64_t)(d + 1) * (uint64_t)(d + 1) * 4;
+    const uint64_t need = wf_off + (uint64_t)(d + 1) * (uint64_t)(d + 1 + L) * 4;
     o.walk_len = (uint32_t)min(m64, 0xFFFFFFFFull);
     if (m64 > 0x3FFFFFFFull || d < 0 || need > A.ws_bytes) {
         if (tid == 0) {
@@ -200,28 +216,33 @@ __device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsig
         __syncthreads();
     }
 
-    // 2. wavefronts, score by score, until the end point (n, m) is reached
+    // 2. wavefronts, score by score, until an end point is reached
     int *wf = (int *)((uint8_t *)tw + wf_off);
     const uint32_t *qw = A.qwords + (A.q_off[qid] >> 4) + qid;
     const int k_end = m - n;
+    if (tid == 0) s_hitk = 0x7FFFFFFF;
+    __syncthreads();
     int found = -1;
     for (int s = 0; s <= d; ++s) {
-        int *cur = wf + (int64_t)s * s + s;
-        const int *prev = wf + (int64_t)(s - 1) * (s - 1) + (s - 1);
+        int *cur = wavefront(wf, s, L);
+        const int *prev = s ? wavefront(wf, s - 1, L) : nullptr;
         bool hit = false;
-        for (int k = -s + tid; k <= s; k += blockDim.x) {
+        for (int k = -s + tid; k <= L + s; k += blockDim.x) {
             int c = -1;
             if (s == 0) {
-                c = 0;
+                c = k >= 0 ? 0 : -1;   // (0, k): the walk entered k bases into its first vertex
             } else {
-                const Pred p = predecessors(prev, s, k, n, m);
+                const Pred p = predecessors(prev, -(s - 1), L + s - 1, k, n, m);
                 c = max(p.sub, max(p.ins, p.del));
             }
             int i = -1;
             if (c >= 0 && c <= n && c + k >= 0 && c + k <= m)
                 i = c + run_length(qw, c, tw, c + k, min(n - c, m - c - k));
             __stcg(cur + k, i);
-            if (k == k_end && i == n) hit = true;
+            if (i == n && (free_end ? n + k >= m - l_last && n + k <= m : k == k_end)) {
+                hit = true;
+                atomicMin(&s_hitk, k);   // several end points: keep the smallest diagonal
+            }
         }
         if (__syncthreads_or(hit)) {
             found = s;
@@ -237,10 +258,11 @@ __device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsig
             return;
         }
         Runs R{A.cigar + (uint64_t)qid * A.cigar_cap, A.cigar_cap, 0u, 0u, 0u};
-        int s = found, k = k_end, i = n;
+        int s = found, k = s_hitk, i = n;
+        o.walk_end = (uint32_t)(n + k);
         while (s > 0) {
-            const int *prev = wf + (int64_t)(s - 1) * (s - 1) + (s - 1);
-            const Pred p = predecessors(prev, s, k, n, m);
+            const int *prev = wavefront(wf, s - 1, L);
+            const Pred p = predecessors(prev, -(s - 1), L + s - 1, k, n, m);
             const int c = max(p.sub, max(p.ins, p.del));
             R.emit(GWFA_CIGAR_EQ, (uint32_t)(i - c));
             if (p.sub == c) {
@@ -257,8 +279,9 @@ __device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsig
             }
             --s;
         }
-        R.emit(GWFA_CIGAR_EQ, (uint32_t)i);   // score 0: equal bases from (0, 0)
+        R.emit(GWFA_CIGAR_EQ, (uint32_t)i);   // score 0: equal bases from (0, k)
         R.flush();
+        o.walk_begin = (uint32_t)k;
         if (R.n <= R.cap)   // emitted end to start: reverse in place
             for (uint32_t a = 0, b = R.n; a + 1 < b; ++a, --b) {
                 const uint32_t t = R.ops[a];
@@ -276,6 +299,7 @@ __global__ void __launch_bounds__(kThreads) cigar_kernel(CigarArgs A) {
     __shared__ uint32_t s_qid, s_base;
     __shared__ unsigned long long s_sum;
     __shared__ uint32_t s_warp[kThreads / 32];
+    __shared__ int s_hitk;
     uint32_t *const tw = (uint32_t *)(A.ws + (uint64_t)blockIdx.x * A.ws_bytes);
     for (;;) {
         if (threadIdx.x == 0) s_qid = atomicAdd(A.head, 1u);
@@ -283,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) cigar_kernel(CigarArgs A) {
         const uint32_t qid = s_qid;
         __syncthreads();
         if (qid >= A.n) return;
-        align_walk(A, qid, tw, s_sum, s_warp, s_base);
+        align_walk(A, qid, tw, s_sum, s_warp, s_base, s_hitk);
         __syncthreads();
     }
 }
@@ -332,11 +356,11 @@ extern "C" int gwfa_cigar_destroy(gwfa_cigar *c) {
 extern "C" int gwfa_cigar_device(gwfa_cigar *c, uint32_t n_queries, const uint32_t *d_words,
                                  const uint64_t *d_q_off, const gwfa_result *d_res,
                                  const uint32_t *d_paths, uint32_t path_cap, const uint32_t *d_path_len,
-                                 uint32_t *d_cigar, uint32_t cigar_cap, gwfa_cigar_result *d_out,
-                                 void *stream) {
+                                 uint32_t *d_cigar, uint32_t cigar_cap, int32_t ends,
+                                 gwfa_cigar_result *d_out, void *stream) {
     if (!c || !d_words || !d_q_off || !d_res || !d_paths || !d_path_len || !d_out) return GWFA_ERR_INVALID;
     if (!d_cigar && cigar_cap) return GWFA_ERR_INVALID;
-    if (path_cap == 0) return GWFA_ERR_INVALID;
+    if (path_cap == 0 || (ends & ~(GWFA_FREE_START | GWFA_FREE_END | GWFA_EXTEND))) return GWFA_ERR_INVALID;
     if (n_queries == 0) return GWFA_OK;
     if (cudaSetDevice(c->g->device) != cudaSuccess) return GWFA_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -352,6 +376,7 @@ extern "C" int gwfa_cigar_device(gwfa_cigar *c, uint32_t n_queries, const uint32
     a.cigar = d_cigar;
     a.cigar_cap = cigar_cap;
     a.out = d_out;
+    a.ends = ends;
     a.ws = c->ws;
     a.ws_bytes = c->ws_bytes;
     a.n = n_queries;

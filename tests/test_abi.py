@@ -33,7 +33,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gw.gwfa_opts) == 28
     assert ctypes.sizeof(gw.gwfa_engine_config) == 128   # 108 bytes of u32 fields, padded to 8
     assert ctypes.sizeof(gw.gwfa_schedule) == 8
-    assert gw.CIGAR_RESULT_DTYPE.itemsize == 16
+    assert gw.CIGAR_RESULT_DTYPE.itemsize == 24
     for name, _ in gw.gwfa_result._fields_:
         assert name in gw.RESULT_DTYPE.names
 

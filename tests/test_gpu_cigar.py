@@ -22,7 +22,7 @@ def _built():
     oracle.build()
 
 
-def traceback_batch(graph, qs, path_cap=4096):
+def traceback_batch(graph, qs, path_cap=4096, ends=0):
     """Exact distances and walks of a batch (traceback engine, max_lag 0)."""
     import torch
     eng = gw.Engine(graph, prune=True)
@@ -30,15 +30,15 @@ def traceback_batch(graph, qs, path_cap=4096):
     plen = torch.zeros(len(qs), dtype=torch.int32, device="cuda")
     eng.set_paths(paths.data_ptr(), path_cap, plen.data_ptr())
     b = gw.DeviceBatch(qs)
-    b.run(eng, traceback=True)
+    b.run(eng, traceback=True, ends=ends)
     torch.cuda.synchronize()
     return eng, b, paths, plen
 
 
-def cigars(graph, b, paths, plen, path_cap=4096, cigar_cap=1024, **kw):
+def cigars(graph, b, paths, plen, path_cap=4096, cigar_cap=1024, ends=0, **kw):
     import torch
     cg = gw.Cigar(graph, **kw)
-    ops, out = cg.run(b, paths, plen, path_cap, cigar_cap)
+    ops, out = cg.run(b, paths, plen, path_cap, cigar_cap, ends=ends)
     torch.cuda.synchronize()
     res = out.cpu().numpy().view(gw.CIGAR_RESULT_DTYPE)
     cg.close()
@@ -149,3 +149,37 @@ def test_failed_queries_are_not_run():
     ops, cr = cigars(graph, b, paths, plen)
     assert cr[3]["status"] == gw.GWFA_ERR_NOT_RUN
     assert np.all(cr["status"][np.arange(8) != 3] == 0)
+
+
+@pytest.mark.parametrize("ends", [1, 2, 3, 4, 5])   # FREE_START, FREE_END, both, EXTEND, EXTEND|FREE_START
+def test_formulation_variants(ends):
+    """With free walk ends the CIGAR aligns the whole query to [walk_begin, walk_end)
+    of sigma(w): the skipped prefix lies in the first vertex, the skipped suffix in the
+    last one, and the cost is the variant distance."""
+    g, qs0 = synth.make_config(1)
+    r = synth.Rng(ends, 3)
+    seqs = []
+    for i in range(len(qs0)):   # cut a few bases from both ends so that free ends matter
+        q = qs0.query(i)
+        a = r.one_int(0, min(len(g.label(int(qs0.v_s[i]))), 20))
+        b = r.one_int(0, min(len(g.label(int(qs0.v_e[i]))), 20))
+        seqs.append(q[a:len(q) - b])
+    qs = queries(seqs, qs0.v_s, qs0.v_e)
+    graph = gw.Graph.from_synth(g)
+    eng, b, paths, plen = traceback_batch(graph, qs, ends=ends)
+    res = b.results()
+    ops, cr = cigars(graph, b, paths, plen, ends=ends)
+    P = paths.view(len(qs), -1).cpu().numpy()
+    L = plen.cpu().numpy()
+    for i in range(len(qs)):
+        assert res[i]["status"] == 0
+        walk = P[i, :L[i]]
+        t = spelled(g, walk)
+        c = cr[i]
+        assert c["status"] == 0, (i, c)
+        assert c["cost"] == res[i]["edit_distance"] == oracle.dp_distance(
+            g, qs.query(i), int(qs.v_s[i]), int(qs.v_e[i]), ends=ends)
+        first, last = len(g.label(int(walk[0]))), len(g.label(int(walk[-1])))
+        assert c["walk_begin"] <= (first if ends & 1 else 0)
+        assert c["walk_end"] >= (len(t) - last if ends & 6 else len(t)) and c["walk_end"] <= len(t)
+        assert apply_cigar(qs.query(i), t[c["walk_begin"]:c["walk_end"]], ops[i, :c["n_ops"]]) == c["cost"]
