@@ -17,7 +17,9 @@ Pins (what ties each function to something other than itself; see tests/):
                      hand-traced work counts (tests/golden/); pruned mode is an
                      upper bound (Sec. 2.5) and equals exact mode when a_diff
                      exceeds every a.  The tie rules for W~ in pruned mode are
-                     a reading of the paper, pinned only by hand-traced cases.
+                     a reading of the paper; their order independence is pinned
+                     by arc-order permutations, against a planted first-spill-
+                     wins rule (GWFA_ORACLE_PLANT_FIRST_TIE, tests only).
   * levenshtein    - textbook values and a python restatement.
   * memory bound   - (evict_lag) removes H~ entries behind the lag: pinned by the
                      upper-bound property (never below the exact distance), by

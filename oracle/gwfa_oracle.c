@@ -482,6 +482,9 @@ int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
         return OR_ERR_INVALID;
     }
     const int extend = (ends & OR_EXTEND) != 0;
+    /* a planted mistake for the tests only: same-generation spills keep the first
+       base instead of the largest, which makes the result depend on the arc order */
+    const int plant_first_tie = getenv("GWFA_ORACLE_PLANT_FIRST_TIE") != NULL;
     int st = og_build(&g, nv, seq, seq_off, na, asrc, adst);
     if (st) { out->distance = st; return st; }
     if (extend) ve = vs;   /* no end vertex */
@@ -556,7 +559,7 @@ int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
                         t->spill_mark = mark;
                         out->spills++;
                         if (dv_push(&Q, u, ku)) { rc = OR_ERR_OOM; goto done; }  /* Q.push */
-                    } else if (t->spill_mark == mark && base + lv > t->base) {
+                    } else if (t->spill_mark == mark && base + lv > t->base && !plant_first_tie) {
                         t->base = base + lv;          /* same-generation tie: larger base */
                     }
                 }
