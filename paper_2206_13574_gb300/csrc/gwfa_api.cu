@@ -114,6 +114,7 @@ const char *gwfa_strerror(int s) {
 int gwfa_graph_create(uint32_t nv, const char *h_seq, const uint64_t *h_seq_off, uint64_t na,
                       const uint32_t *h_arc_src, const uint32_t *h_arc_dst, int device,
                       gwfa_graph **out) {
+    gwfa::Range range_("gwfa_graph_create");
     if (!out || !h_seq_off || (nv > 0 && !h_seq) || (na > 0 && (!h_arc_src || !h_arc_dst)))
         return GWFA_ERR_INVALID;
     *out = nullptr;
@@ -243,6 +244,7 @@ int gwfa_align_path(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t v
 static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t vs, uint32_t ve,
                        const gwfa_opts &o, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
                        uint32_t *path_len) {
+    gwfa::Range range_(o.traceback ? "gwfa_align_path" : "gwfa_align");
     if (!g || !out || (n > 0 && !h_q)) return GWFA_ERR_INVALID;
     memset(out, 0, sizeof(*out));
     out->edit_distance = -1;
@@ -400,6 +402,7 @@ static int engine_retry_capacity(gwfa_engine *e, uint64_t n) {
 }
 
 int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_engine **out) {
+    gwfa::Range range_("gwfa_engine_create");
     if (!g || !cfg || !out) return GWFA_ERR_INVALID;
     *out = nullptr;
     if (cfg->n_tiers < 1 || cfg->n_tiers > GWFA_MAX_TIERS) return GWFA_ERR_INVALID;
@@ -665,6 +668,7 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
                             const uint64_t *d_q_off, const uint32_t *d_vs, const uint32_t *d_ve,
                             const uint32_t *d_order, const gwfa_schedule *sched, const int32_t *d_status,
                             const gwfa_opts *opts, gwfa_result *d_out, void *stream) {
+    gwfa::Range range_("gwfa_align_batch_device");
     if (!e || !d_words || !d_q_off || !d_vs || !d_ve || !d_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
     if (o.max_lag < 0 || (o.traceback && o.max_lag != 0) || !ends_ok(o)) return GWFA_ERR_INVALID;
@@ -683,6 +687,7 @@ int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t
                      const uint32_t *h_vs, const uint32_t *h_ve, const uint32_t *h_order,
                      const gwfa_schedule *sched, const gwfa_opts *opts, gwfa_result *h_out, void *stream) {
     if (!e || !h_q_off || !h_vs || !h_ve || !h_out) return GWFA_ERR_INVALID;
+    gwfa::Range range_("gwfa_align_batch");
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
     if (o.max_lag < 0 || (o.traceback && o.max_lag != 0) || !ends_ok(o)) return GWFA_ERR_INVALID;
     if ((o.max_lag > 0 || o.traceback) && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
@@ -709,18 +714,24 @@ int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t
     int32_t *d_status = c.take<int32_t>((uint64_t)n * 4);
     uint32_t *d_words = c.take<uint32_t>(words_for(n, nb) * 4);
     gwfa_result *d_out = c.take<gwfa_result>((uint64_t)n * sizeof(gwfa_result));
+    nvtxRangePushA("copy in + pack");
     st = cuda_status(cudaMemcpyAsync(d_q, h_q, nb, cudaMemcpyHostToDevice, s));
     if (!st) st = cuda_status(cudaMemcpyAsync(d_off, h_q_off, (uint64_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
     if (!st) st = cuda_status(cudaMemcpyAsync(d_vs, h_vs, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
     if (!st) st = cuda_status(cudaMemcpyAsync(d_ve, h_ve, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
     if (!st && h_order) st = cuda_status(cudaMemcpyAsync(d_order, h_order, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
     if (!st) st = cuda_status(gwfa::launch_pack(n, d_q, d_off, d_words, d_status, s));
+    nvtxRangePop();
+    nvtxRangePushA("alignment tiers");
     if (!st)
         st = run_tiers(e, n, d_words, d_off, d_vs, d_ve, h_order ? d_order : nullptr, sched, d_status, o,
                        d_out, s);
+    nvtxRangePop();
     if (!st) e->last_launches += 1;
+    nvtxRangePushA("copy out + wait");
     if (!st) st = cuda_status(cudaMemcpyAsync(h_out, d_out, (uint64_t)n * sizeof(gwfa_result), cudaMemcpyDeviceToHost, s));
     if (!st) st = cuda_status(cudaStreamSynchronize(s));
+    nvtxRangePop();
     return st;
 }
 

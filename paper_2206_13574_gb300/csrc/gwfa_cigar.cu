@@ -358,6 +358,7 @@ extern "C" int gwfa_cigar_device(gwfa_cigar *c, uint32_t n_queries, const uint32
                                  const uint32_t *d_paths, uint32_t path_cap, const uint32_t *d_path_len,
                                  uint32_t *d_cigar, uint32_t cigar_cap, int32_t ends,
                                  gwfa_cigar_result *d_out, void *stream) {
+    gwfa::Range range_("gwfa_cigar_device");
     if (!c || !d_words || !d_q_off || !d_res || !d_paths || !d_path_len || !d_out) return GWFA_ERR_INVALID;
     if (!d_cigar && cigar_cap) return GWFA_ERR_INVALID;
     if (path_cap == 0 || (ends & ~(GWFA_FREE_START | GWFA_FREE_END | GWFA_EXTEND))) return GWFA_ERR_INVALID;

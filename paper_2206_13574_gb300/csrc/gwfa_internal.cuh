@@ -6,9 +6,20 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gwfa.h"
 
 namespace gwfa {
+
+// Host-side profiler range (NVTX): names a phase of a library call on the timeline
+// of a profiler that is attached; a few nanoseconds when none is.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // A tile groups the 8 diagonals k = 8*kb .. 8*kb+7 of one vertex: its 8 offsets
 // H~_{v,k} are one 32-byte sector (exact mode) and are processed by 8 adjacent

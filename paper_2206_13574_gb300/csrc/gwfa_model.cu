@@ -446,6 +446,7 @@ int gwfa_model_gradient_device(gwfa_model *m, uint32_t n, const float *d_feat, c
 int gwfa_model_train_device(gwfa_model *m, uint32_t n, const float *d_feat, const float *d_target,
                             uint32_t steps, uint32_t batch, float lr, uint64_t seed, float *h_losses,
                             void *stream) {
+    gwfa::Range range_("gwfa_model_train_device");
     if (!m || !d_feat || !d_target || n == 0 || steps == 0 || batch == 0 || !(lr > 0.f))
         return GWFA_ERR_INVALID;
     std::lock_guard<std::mutex> lk(m->mu);
