@@ -86,6 +86,36 @@ def test_overflow_requeues_to_large_slabs(c2):
     srv.close()
 
 
+def test_model_admission_avoids_requeues(c2):
+    """Admission by predicted memory: with a trained cost model attached, requests the
+    model expects to overflow the small slabs go straight to the large ones, so fewer
+    are re-queued than with length-only admission; results are unchanged."""
+    from paper_2206_13574_gb300 import costmodel
+    g, qs, graph = c2
+    eng = gw.Engine(graph)
+    model = gw.CostModel(graph, seed=3)
+    feat, tgt, _ = costmodel.collect(model, eng, qs.subset(np.arange(200)))
+    costmodel.fit(model, feat, tgt, steps=600, batch=128, lr=3e-3)
+    test = list(range(200, 320))
+    ref = eng.align_batch(qs.seq, qs.off, qs.v_s, qs.v_e)
+    requeued = {}
+    for name, m in (("length", None), ("model", model)):
+        cfg = gw.gwfa_server_config()
+        gw.load().gwfa_server_default_config(graph.handle, cfg)
+        cfg.ctas_small, cfg.log2_small = 32, 11
+        cfg.ctas_big, cfg.log2_big = 16, 17
+        cfg.big_length = 10 ** 9                    # without a model: everything to class 0
+        srv = gw.Server(graph, cfg, model=m)
+        res = [srv.wait(srv.submit(qs.query(i), int(qs.v_s[i]), int(qs.v_e[i]))) for i in test]
+        for i, r in zip(test, res):
+            assert r["status"] == 0
+            for k in KEYS:
+                assert r[k] == int(ref[i][k]), (name, i, k)
+        requeued[name] = srv.stats()["requeued"]
+        srv.close()
+    assert requeued["length"] > 0 and requeued["model"] < requeued["length"], requeued
+
+
 def test_idle_exit_and_restart(c2):
     g, qs, graph = c2
     cfg = gw.gwfa_server_config()
