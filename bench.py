@@ -128,17 +128,17 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_reference(args, g, qs, sample_s: float):
+def cpu_reference(args, g, qs, sample_s: float, cores: int | None = None):
     """Time the oracle (Alg. 1-3 in C) on a bounded sample: one query per thread."""
     import oracle
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = cores or os.cpu_count() or 1
     rng = np.random.default_rng(12345)
     order = rng.permutation(len(qs))
     ga = oracle.GraphArgs(g)
     # grow the sample until it costs about `sample_s` seconds
     done, bases, t_total = 0, 0, 0.0
-    chunk = max(cores * 8, 64)
+    chunk = max(cores * 8, 8)
     t0 = time.perf_counter()
     while done < len(order) and time.perf_counter() - t0 < sample_s:
         idx = order[done:done + chunk]
@@ -454,6 +454,8 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_reference(args, g, qs, sample_s=args.cpu_sample_s)
+        one = cpu_reference(args, g, qs, sample_s=max(2.0, args.cpu_sample_s / 4), cores=1)
+        cpu["single_core"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
 
     if rank == 0:
         line = {
