@@ -91,7 +91,8 @@ typedef struct {
  *   n_scores      number of GwfExtend calls (= edit_distance + 1 on success);
  *   cells         sum over scores of |Q| after GwfExtend (diagonals extended);
  *   peak_frontier max over scores of |Q| after GwfExtend;
- *   visited       distinct diagonals (v, k) ever inserted into H~;
+ *   visited       insertions of diagonals (v, k) into H~: the distinct diagonals ever
+ *                 inserted, unless the memory bound removed some that came back;
  *   pruned        diagonals dropped by GwfPrune, summed over scores;
  *   spills        diagonals inserted by the arc loop of GwfExtend.
  */
@@ -179,7 +180,9 @@ typedef struct gwfa_engine gwfa_engine;
  *                  n_wide queries of the schedule (gwfa_schedule), so the heaviest
  *                  queries start at once on slabs that fit them instead of forming a
  *                  tail of overflow re-runs; their overflows go to the retry tiers
- *   threads        threads per CTA (multiple of 32, 64..512); 0 = 128
+ *   threads        threads per CTA (multiple of 32, 64..1024; above 512 a CTA
+ *                  takes half an SM: for the few heaviest queries, e.g. the huge
+ *                  class, whose own latency bounds a batch); 0 = 128
  *   max_queries, max_bases  sizes of the engine's staging buffers for the
  *                  host-buffer entry point (grown on demand)
  */

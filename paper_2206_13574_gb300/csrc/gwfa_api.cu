@@ -407,13 +407,13 @@ int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_
     *out = nullptr;
     if (cfg->n_tiers < 1 || cfg->n_tiers > GWFA_MAX_TIERS) return GWFA_ERR_INVALID;
     const uint32_t threads = cfg->threads ? cfg->threads : 128;
-    if (threads % 32 || threads < 64 || threads > 512) return GWFA_ERR_INVALID;
+    if (threads % 32 || threads < 64 || threads > 1024) return GWFA_ERR_INVALID;
     for (uint32_t t = 0; t < cfg->n_tiers + 2; ++t) {
         const gwfa_tier &tt = t < cfg->n_tiers ? cfg->tiers[t] : (t == cfg->n_tiers ? cfg->wide : cfg->huge);
         if (t >= cfg->n_tiers && tt.ctas == 0) continue;   // class not used
         const uint32_t th = tt.threads;
         if (tt.ctas == 0 || tt.log2_tiles < 8 || tt.log2_tiles > gwfa::kMaxLog2Tiles ||
-            (th && (th % 32 || th < 64 || th > 512)))
+            (th && (th % 32 || th < 64 || th > 1024)))
             return GWFA_ERR_INVALID;
     }
     int st = cuda_status(cudaSetDevice(g->device));

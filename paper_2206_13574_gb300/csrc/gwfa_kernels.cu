@@ -896,8 +896,9 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
     __syncthreads();
 }
 
+// The persistent loop of a CTA: pull a query id, run its score loop, repeat.
 template <bool P>
-__global__ void __launch_bounds__(512, 4) align_kernel(TierArgs A) {
+__device__ __forceinline__ void align_queries(const TierArgs &A) {
     __shared__ Sh sh;
     const Slab<P> s = carve<P>(A.slabs + (uint64_t)blockIdx.x * A.slab_bytes, A.log2cap);
     const uint32_t count = A.list_count ? *A.list_count : A.count_val;
@@ -912,6 +913,19 @@ __global__ void __launch_bounds__(512, 4) align_kernel(TierArgs A) {
         if (qid == 0xFFFFFFFFu) break;
         align_one<P>(A, s, sh, qid);
     }
+}
+
+// Up to 512 threads, 4 CTAs per SM at 32 registers: the throughput shape.
+template <bool P>
+__global__ void __launch_bounds__(512, 4) align_kernel(TierArgs A) {
+    align_queries<P>(A);
+}
+
+// 1024 threads, 2 CTAs per SM at the same 32 registers: twice the groups on one
+// query, for the few heaviest queries whose own latency bounds a batch.
+template <bool P>
+__global__ void __launch_bounds__(1024, 2) align_kernel_wide(TierArgs A) {
+    align_queries<P>(A);
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
@@ -1072,8 +1086,13 @@ __global__ void slab_init_kernel(uint8_t *slabs, uint64_t slab_bytes, uint32_t n
 
 cudaError_t launch_align(const TierArgs &a, bool prune, uint32_t ctas, uint32_t threads,
                          cudaStream_t st) {
-    if (prune) align_kernel<true><<<ctas, threads, 0, st>>>(a);
-    else align_kernel<false><<<ctas, threads, 0, st>>>(a);
+    if (threads > 512) {
+        if (prune) align_kernel_wide<true><<<ctas, threads, 0, st>>>(a);
+        else align_kernel_wide<false><<<ctas, threads, 0, st>>>(a);
+    } else {
+        if (prune) align_kernel<true><<<ctas, threads, 0, st>>>(a);
+        else align_kernel<false><<<ctas, threads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

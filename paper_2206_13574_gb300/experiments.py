@@ -138,12 +138,12 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
     total = base.tiers[0].ctas
     wide_log2, huge_log2 = 20, 23
 
-    def engine(wide: int = 0, huge: int = 0):
+    def engine(wide: int = 0, huge: int = 0, huge_threads: int = 1024):
         cfg = gw.default_config(gr4)
         cfg.tiers[1].ctas, cfg.tiers[1].log2_tiles = 152, 20
         cfg.tiers[2].ctas, cfg.tiers[2].log2_tiles = 19, 23
         cfg.wide.ctas, cfg.wide.log2_tiles, cfg.wide.threads = wide, wide_log2, 512
-        cfg.huge.ctas, cfg.huge.log2_tiles, cfg.huge.threads = huge, huge_log2, 512
+        cfg.huge.ctas, cfg.huge.log2_tiles, cfg.huge.threads = huge, huge_log2, huge_threads
         return gw.Engine(gr4, config=cfg)
 
     probe = engine(1, 1).config
@@ -157,15 +157,15 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
            "learned_huge": [int(l_huge), int(h_ctas), huge_log2], "learned_wide": [int(l_wide), int(w_ctas), wide_log2],
            "time_coeffs_us": list(coeffs)}
     ref = None
-    plans = {"plain_fifo": (None, 0, 0, 0, 0),
-             "plain_longest_first": (np.argsort(-q4.lengths(), kind="stable"), 0, 0, 0, 0),
-             "learned_wide_only": (*gw.plan_schedule(pred, int(0.75 * (1 << base.tiers[0].log2_tiles)))[::2],
-                                   0, 0, 0),
-             "learned": (l_order, l_huge, l_wide, h_ctas, w_ctas)}
-    o2, nw2 = plans["learned_wide_only"][:2]
-    plans["learned_wide_only"] = (o2, 0, nw2, 0, costmodel.wide_ctas(pred, o2, nw2, total, coeffs))
-    for name, (order, nh, nw, hc, wc) in plans.items():
-        eng = engine(wc, hc)
+    # (order, n_huge, n_wide, huge CTAs, wide CTAs, threads per huge CTA)
+    plans = {"plain_fifo": (None, 0, 0, 0, 0, 512),
+             "plain_longest_first": (np.argsort(-q4.lengths(), kind="stable"), 0, 0, 0, 0, 512)}
+    o2, _, nw2 = gw.plan_schedule(pred, int(0.75 * (1 << base.tiers[0].log2_tiles)))
+    plans["learned_wide_only"] = (o2, 0, nw2, 0, costmodel.wide_ctas(pred, o2, nw2, total, coeffs), 512)
+    plans["learned_huge_512_threads"] = (l_order, l_huge, l_wide, h_ctas, w_ctas, 512)
+    plans["learned"] = (l_order, l_huge, l_wide, h_ctas, w_ctas, 1024)
+    for name, (order, nh, nw, hc, wc, hth) in plans.items():
+        eng = engine(wc, hc, hth)
         b = gw.DeviceBatch(q4, order=None if order is None else np.asarray(order, np.uint32))
         b.run(eng, n_wide=nw, n_huge=nh)
         t = _timed_run(eng, b, n_wide=nw, n_huge=nh)
@@ -177,7 +177,8 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
         out[name] = {"s": t, "gbp_per_s": float(q4.lengths()[r["status"] == 0].sum()) / t / 1e9,
                      "tier0_overflows": int(retries[0]), "tier1_overflows": int(retries[1]),
                      "n_huge": int(nh), "n_wide": int(nw), "huge_ctas": int(hc), "wide_ctas": int(wc),
-                     "ok": int((r["status"] == 0).sum()), "slab_bytes": eng.device_bytes}
+                     "huge_threads": int(hth), "ok": int((r["status"] == 0).sum()),
+                     "slab_bytes": eng.device_bytes, "slowest_query_ms": float(r["device_us"].max() / 1e3)}
         eng.close()
     # where the time goes: the heaviest queries' own CTA times against the batch
     top = np.argsort(-ref["device_us"].astype(np.float64))[:8]

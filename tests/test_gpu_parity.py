@@ -174,6 +174,23 @@ def test_concurrent_classes_do_not_change_results(tiers):
             assert np.array_equal(base[f][ok], res[f][ok]), f
 
 
+def test_1024_thread_ctas_do_not_change_results():
+    """Tiers and the huge class at 1024 threads per CTA (half an SM each) give the same
+    results as the default 512-thread engine."""
+    g, qs = synth.make_config(2, n_queries=300)
+    graph = gw.Graph.from_synth(g)
+    base = gw.Engine(graph).align_batch(qs.seq, qs.off, qs.v_s, qs.v_e)
+    cfg = gw.default_config(graph)
+    cfg.tiers[0].ctas, cfg.tiers[0].threads = 96, 1024
+    cfg.huge.ctas, cfg.huge.log2_tiles, cfg.huge.threads = 6, 18, 1024
+    eng = gw.Engine(graph, config=cfg)
+    order = np.argsort(-qs.lengths(), kind="stable").astype(np.uint32)
+    res = eng.align_batch(qs.seq, qs.off, qs.v_s, qs.v_e, order=order, n_huge=12)
+    for f in gw.RESULT_DTYPE.names:
+        if f != "device_us":
+            assert np.array_equal(base[f], res[f]), f
+
+
 def test_capacity_error_without_retry_tier():
     g, qs = synth.make_config(2, n_queries=50)
     graph = gw.Graph.from_synth(g)
