@@ -97,10 +97,10 @@ def config3(n_pruned: int = 2000, n_exact: int = 200, a_diff: int = 1000) -> dic
             "work_ratio_exact_over_pruned": float(ex["cells"][ok].sum() / max(prs["cells"][ok].sum(), 1))}
 
 
-def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_plain: int = 100) -> dict:
-    """Large graph (50 Mb, lognormal 1-100 kb queries, 0.1-10% divergence), exact:
-    plain schedules (input order, longest first) against the learned plan of a cost
-    model trained on config-2 and config-3-graph logs (other graphs)."""
+def _trained_model(n_train_c2: int = 3000, n_train_c3: int = 300):
+    """Cost model trained on wave logs of config-2 queries and of queries on the
+    config-3 graph (graphs other than the large one it is used on); also the fitted
+    per-score / per-cell time coefficients."""
     import paper_2206_13574_gb300 as gw
     from paper_2206_13574_gb300 import costmodel, synth
     import torch
@@ -127,6 +127,16 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
     feat = torch.cat(feats)
     tgt = torch.cat(tgts)
     costmodel.fit(m2, feat, tgt, steps=2000, batch=512, lr=3e-3)
+    return m2, coeffs
+
+
+def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_plain: int = 100) -> dict:
+    """Large graph (50 Mb, lognormal 1-100 kb queries, 0.1-10% divergence), exact:
+    plain schedules (input order, longest first) against the learned plan of a cost
+    model trained on config-2 and config-3-graph logs (other graphs)."""
+    import paper_2206_13574_gb300 as gw
+    from paper_2206_13574_gb300 import costmodel, synth
+    m2, coeffs = _trained_model(n_train_c2, n_train_c3)
     # the large workload
     g4, q4 = synth.make_config(4, n_queries=n)
     gr4 = gw.Graph.from_synth(g4)
@@ -202,7 +212,8 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
 
 
 def serving(n_pool: int = 3000, rates=(1000.0, 5000.0, 20000.0), duration: float = 1.0,
-            plain_rate: float = 100.0, plain_duration: float = 2.0, cfg: int = 2) -> dict:
+            plain_rate: float = 100.0, plain_duration: float = 2.0, cfg: int = 2,
+            with_model: bool = False) -> dict:
     """A resident graph, Poisson arrivals: the continuous-batching server's p50/p99 at
     several rates, and the plain one-query-at-a-time path at a low rate.  cfg 2: the
     config-2 graph and queries; cfg 5: the 50 Mb config-4 graph with its lognormal
@@ -222,6 +233,19 @@ def serving(n_pool: int = 3000, rates=(1000.0, 5000.0, 20000.0), duration: float
         out[f"server_lambda_{int(lam)}"], _ = sv.run_server(srv, qs, arr, idx)
     out["server_stats"] = srv.stats()
     srv.close()
+    if with_model:
+        # admission by the cost model's predicted memory instead of the query length
+        from paper_2206_13574_gb300 import costmodel
+        m_src, _ = _trained_model()
+        model = gw.CostModel(graph, seed=1)
+        costmodel.transfer(m_src, model)
+        srvm = gw.Server(graph, model=model)
+        for lam in rates:
+            arr = synth.poisson_arrivals(lam, duration, seed=int(lam))
+            idx = np.arange(len(arr)) % n_pool
+            out[f"model_server_lambda_{int(lam)}"], _ = sv.run_server(srvm, qs, arr, idx)
+        out["model_server_stats"] = srvm.stats()
+        srvm.close()
     arr = synth.poisson_arrivals(plain_rate, plain_duration, seed=3)
     idx = np.arange(len(arr)) % n_pool
     out[f"plain_lambda_{int(plain_rate)}"], _ = sv.run_plain(graph, qs, arr, idx)
@@ -238,6 +262,6 @@ if __name__ == "__main__":
     t0 = time.time()
     res = {"config3": config3, "scheduler": scheduler, "serving": serving,
            "serving5": lambda: serving(n_pool=2000, rates=(250.0, 1000.0, 4000.0), duration=1.0,
-                                       plain_rate=10.0, plain_duration=3.0, cfg=5)}[which]()
+                                       plain_rate=10.0, plain_duration=3.0, cfg=5, with_model=True)}[which]()
     res["wall_s"] = time.time() - t0
     print(json.dumps(res))
