@@ -417,6 +417,7 @@ int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_
             return GWFA_ERR_INVALID;
     }
     int st = cuda_status(cudaSetDevice(g->device));
+    if (!st) st = cuda_status(gwfa::preload_kernels());
     if (st) return st;
     gwfa_engine *e = new (std::nothrow) gwfa_engine();
     if (!e) return GWFA_ERR_OOM;

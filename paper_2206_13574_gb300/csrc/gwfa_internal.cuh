@@ -168,6 +168,7 @@ cudaError_t launch_fill(void *p, uint64_t bytes, cudaStream_t st);
 cudaError_t launch_slab_init(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_slabs, uint32_t log2cap,
                              bool prune, cudaStream_t st);
 int align_occupancy(bool prune, uint32_t threads, int *blocks_per_sm);
+cudaError_t preload_kernels();
 cudaError_t launch_server(const ServerArgs &a, bool prune, uint32_t ctas, uint32_t threads,
                           uint32_t smem_bytes, cudaStream_t st);
 

@@ -1138,6 +1138,19 @@ cudaError_t launch_slab_init(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_sla
     return cudaGetLastError();
 }
 
+// Load the alignment kernels into the context now.  With lazy module loading a
+// kernel's code is loaded at its first launch, and that load can wait for kernels
+// already running; an engine runs several of them side by side (its classes
+// beside tier 0), so it touches them all before the first one starts.
+cudaError_t preload_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, align_kernel<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, align_kernel<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, align_kernel_wide<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, align_kernel_wide<true>);
+    return e;
+}
+
 int align_occupancy(bool prune, uint32_t threads, int *blocks_per_sm) {
     cudaError_t e = prune
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, align_kernel<true>, (int)threads, 0)
