@@ -2,6 +2,7 @@
 
     python -m paper_2206_13574_gb300.experiments config3     # cyclic graph: exact vs lag-pruned
     python -m paper_2206_13574_gb300.experiments scheduler   # large graph: learned vs plain scheduling
+    python -m paper_2206_13574_gb300.experiments scheduler100k   # the same at 100k queries (two plans)
     python -m paper_2206_13574_gb300.experiments serving     # server vs one-query-at-a-time
     python -m paper_2206_13574_gb300.experiments serving5    # the same on the 50 Mb graph (config 5)
 
@@ -130,7 +131,8 @@ def _trained_model(n_train_c2: int = 3000, n_train_c3: int = 300):
     return m2, coeffs
 
 
-def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_plain: int = 100) -> dict:
+def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_plain: int = 100,
+              only=None) -> dict:
     """Large graph (50 Mb, lognormal 1-100 kb queries, 0.1-10% divergence), exact:
     plain schedules (input order, longest first) against the learned plan of a cost
     model trained on config-2 and config-3-graph logs (other graphs)."""
@@ -174,6 +176,8 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
     plans["learned_wide_only"] = (o2, 0, nw2, 0, costmodel.wide_ctas(pred, o2, nw2, total, coeffs), 512)
     plans["learned_huge_512_threads"] = (l_order, l_huge, l_wide, h_ctas, w_ctas, 512)
     plans["learned"] = (l_order, l_huge, l_wide, h_ctas, w_ctas, 1024)
+    if only is not None:
+        plans = {k: v for k, v in plans.items() if k in only}
     for name, (order, nh, nw, hc, wc, hth) in plans.items():
         eng = engine(wc, hc, hth)
         b = gw.DeviceBatch(q4, order=None if order is None else np.asarray(order, np.uint32))
@@ -195,16 +199,17 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
     out["slowest_queries"] = [{"len": int(q4.lengths()[i]), "us": int(ref["device_us"][i]),
                                "cells": int(ref["cells"][i]), "visited": int(ref["visited"][i])} for i in top]
     # S4 on the same workload: the plain path, one synchronous launch per query
-    rng = np.random.default_rng(4)
-    sidx = rng.choice(len(q4), size=min(n_plain, len(q4)), replace=False)
-    t0 = time.perf_counter()
-    for i in sidx:
-        r = gr4.align(q4.query(int(i)), int(q4.v_s[i]), int(q4.v_e[i]))
-        assert r["edit_distance"] == int(ref["edit_distance"][i])
-    tp = time.perf_counter() - t0
-    out["plain_per_query"] = {"queries": int(len(sidx)), "s": tp,
-                              "gbp_per_s": float(q4.lengths()[sidx].sum()) / tp / 1e9,
-                              "ms_per_query": tp / len(sidx) * 1e3}
+    if n_plain:
+        rng = np.random.default_rng(4)
+        sidx = rng.choice(len(q4), size=min(n_plain, len(q4)), replace=False)
+        t0 = time.perf_counter()
+        for i in sidx:
+            r = gr4.align(q4.query(int(i)), int(q4.v_s[i]), int(q4.v_e[i]))
+            assert r["edit_distance"] == int(ref["edit_distance"][i])
+        tp = time.perf_counter() - t0
+        out["plain_per_query"] = {"queries": int(len(sidx)), "s": tp,
+                                  "gbp_per_s": float(q4.lengths()[sidx].sum()) / tp / 1e9,
+                                  "ms_per_query": tp / len(sidx) * 1e3}
     out["cells"] = int(ref["cells"].sum())
     out["spearman_pred_cells"] = costmodel.spearman(pred[:, 3], np.log1p(ref["cells"].astype(np.float64)))
     out["r2_log_cells"] = float(costmodel.r2(pred[:, 3:4], np.log1p(ref["cells"].astype(np.float64))[:, None])[0])
@@ -261,6 +266,7 @@ if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "config3"
     t0 = time.time()
     res = {"config3": config3, "scheduler": scheduler, "serving": serving,
+           "scheduler100k": lambda: scheduler(n=100_000, n_plain=0, only=("plain_fifo", "learned")),
            "serving5": lambda: serving(n_pool=2000, rates=(250.0, 1000.0, 4000.0), duration=1.0,
                                        plain_rate=10.0, plain_duration=3.0, cfg=5, with_model=True)}[which]()
     res["wall_s"] = time.time() - t0
