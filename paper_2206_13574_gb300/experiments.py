@@ -165,7 +165,7 @@ def scheduler(n: int = 5000, n_train_c2: int = 3000, n_train_c3: int = 300, n_pl
     h_ctas = min(l_huge, 32)
     w_ctas = costmodel.wide_ctas(pred, l_order, l_wide, total, coeffs, first=l_huge)
     out = {"workload": f"config4: 50 Mb graph, {n} lognormal 1-100 kb queries, 0.1-10% divergence, exact",
-           "train": f"{len(q2)} config-2 + {len(q3)} config-3-graph queries, 2000 Adam steps",
+           "train": f"{n_train_c2} config-2 + {n_train_c3} config-3-graph queries, 2000 Adam steps",
            "learned_huge": [int(l_huge), int(h_ctas), huge_log2], "learned_wide": [int(l_wide), int(w_ctas), wide_log2],
            "time_coeffs_us": list(coeffs)}
     ref = None
