@@ -469,6 +469,32 @@ static inline int64_t lcp(const uint8_t *q, int64_t n, int64_t i, const uint8_t 
  * distance stays an upper bound of the exact one. */
 #define KEEP_MARK (UINT64_MAX - 1)
 
+/* The removal step itself: keep the entries of `keep` (the new Q) and those whose
+ * a = i + W~ lags amax by less than lag (or by at most lag, with the planted `le`
+ * mistake); count the others in out->evicted. */
+static int evict(hmap *H, const dvec *keep, int64_t amax, int64_t lag, int le, oracle_stats *out) {
+    for (uint64_t p = 0; p < keep->n; ++p) hm_find(H, dkey(keep->a[p].v, keep->a[p].k))->spill_mark = KEEP_MARK;
+    hmap H2 = {0};
+    if (hm_init(&H2, H->cap)) return OR_ERR_OOM;
+    for (uint64_t x = 0; x < H->cap; ++x) {
+        ent_t *e = &H->e[x];
+        if (e->key == EMPTY_KEY) continue;
+        int64_t k = (int32_t)(uint32_t)(e->key & 0xFFFFFFFFu);
+        int64_t a = (k + e->j) + (e->base + e->j);   /* i + W~ */
+        if (e->spill_mark == KEEP_MARK || amax - a < lag || (le && amax - a == lag)) {
+            ent_t *c = hm_insert(&H2, e->key);
+            if (!c) { free(H2.e); return OR_ERR_OOM; }
+            *c = *e;
+            c->spill_mark = UINT64_MAX;
+        } else {
+            out->evicted++;
+        }
+    }
+    free(H->e);
+    *H = H2;
+    return OR_OK;
+}
+
 int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
                    uint64_t na, const uint32_t *asrc, const uint32_t *adst,
                    const char *qs, uint64_t n, uint32_t vs, uint32_t ve,
@@ -485,6 +511,12 @@ int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
     /* a planted mistake for the tests only: same-generation spills keep the first
        base instead of the largest, which makes the result depend on the arc order */
     const int plant_first_tie = getenv("GWFA_ORACLE_PLANT_FIRST_TIE") != NULL;
+    /* planted mistakes in the memory bound, for the tests only (each must change a
+       hand-traced counter): keep an entry lagging by exactly evict_lag; keep by Q as
+       GwfExtend left it instead of the new Q; evict before GwfExpand instead of after */
+    const int plant_evict_le = getenv("GWFA_ORACLE_PLANT_EVICT_LE") != NULL;
+    const int plant_evict_oldq = getenv("GWFA_ORACLE_PLANT_EVICT_OLDQ") != NULL;
+    const int plant_evict_before = getenv("GWFA_ORACLE_PLANT_EVICT_BEFORE") != NULL;
     int st = og_build(&g, nv, seq, seq_off, na, asrc, adst);
     if (st) { out->distance = st; return st; }
     if (extend) ve = vs;   /* no end vertex */
@@ -504,7 +536,7 @@ int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
 
     hmap H = {0}, Hp = {0};
     int64_t inserted = 0;   /* insertions into H~ */
-    dvec Q = {0}, Qp = {0};
+    dvec Q = {0}, Qp = {0}, Qx = {0};
     int rc = OR_OK;
     if (hm_init(&H, 1 << 12) || hm_init(&Hp, 1 << 12)) { rc = OR_ERR_OOM; goto done; }
 
@@ -585,6 +617,12 @@ int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
         if (max_score >= 0 && d >= max_score) { rc = OR_ERR_SCORE_LIMIT; goto done; }
         d = d + 1;                                    /* d <- d + 1 */
 
+        if (plant_evict_oldq) {                     /* planted mistake: remember Q after GwfExtend */
+            Qx.n = 0;
+            for (uint64_t p = 0; p < Q.n; ++p)
+                if (dv_push(&Qx, Q.a[p].v, Q.a[p].k)) { rc = OR_ERR_OOM; goto done; }
+        }
+
         /* ---- GwfPrune (Alg. 4), between d <- d+1 and GwfExpand ---- */
         int64_t amax = 0;
         if (a_diff > 0) {
@@ -607,6 +645,11 @@ int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
                 if (Qp.n < Q.n) { out->is_upper_bound = 1; out->pruned += (int64_t)(Q.n - Qp.n); }
                 dvec tq = Q; Q = Qp; Qp = tq;
             }
+        }
+
+        if (evict_lag > 0 && d % evict_every == 0 && plant_evict_before) {   /* planted mistake */
+            rc = evict(&H, &Q, amax, evict_lag, plant_evict_le, out);
+            if (rc) goto done;
         }
 
         /* ---- GwfExpand (Alg. 3) ---- */
@@ -658,33 +701,23 @@ int oracle_gwfa_ex(uint32_t nv, const char *seq, const uint64_t *seq_off,
         if (Q.n == 0) { rc = OR_ERR_EMPTY_FRONTIER; goto done; }
 
         /* ---- memory bound on H~ (see above) ---- */
-        if (evict_lag > 0 && d % evict_every == 0) {
-            for (uint64_t p = 0; p < Q.n; ++p) hm_find(&H, dkey(Q.a[p].v, Q.a[p].k))->spill_mark = KEEP_MARK;
-            hmap H2 = {0};
-            if (hm_init(&H2, H.cap)) { rc = OR_ERR_OOM; goto done; }
-            for (uint64_t x = 0; x < H.cap; ++x) {
-                ent_t *e = &H.e[x];
-                if (e->key == EMPTY_KEY) continue;
-                int64_t k = (int32_t)(uint32_t)(e->key & 0xFFFFFFFFu);
-                int64_t a = (k + e->j) + (e->base + e->j);   /* i + W~ */
-                if (e->spill_mark == KEEP_MARK || amax - a < evict_lag) {
-                    ent_t *c = hm_insert(&H2, e->key);
-                    if (!c) { free(H2.e); rc = OR_ERR_OOM; goto done; }
-                    *c = *e;
-                    c->spill_mark = UINT64_MAX;
-                } else {
-                    out->evicted++;
-                }
+        if (evict_lag > 0 && d % evict_every == 0 && !plant_evict_before) {
+            rc = evict(&H, plant_evict_oldq ? &Qx : &Q, amax, evict_lag, plant_evict_le, out);
+            if (rc) goto done;
+            if (plant_evict_oldq) {                 /* the new Q loses what that removed */
+                uint64_t m = 0;
+                for (uint64_t p = 0; p < Q.n; ++p)
+                    if (hm_find(&H, dkey(Q.a[p].v, Q.a[p].k))) Q.a[m++] = Q.a[p];
+                Q.n = m;
+                if (Q.n == 0) { rc = OR_ERR_EMPTY_FRONTIER; goto done; }
             }
-            free(H.e);
-            H = H2;
         }
     }
     out->distance = d;
 done:
     out->visited = inserted;
     if (rc != OR_OK) out->distance = rc;
-    free(H.e); free(Hp.e); free(Q.a); free(Qp.a); free(q); og_free(&g);
+    free(H.e); free(Hp.e); free(Q.a); free(Qp.a); free(Qx.a); free(q); og_free(&g);
     return rc;
 }
 

@@ -54,14 +54,17 @@ def test_handtraced_cases_plain_and_batched():
         g = synth.Graph.from_lists(c["labels"], [tuple(a) for a in c["arcs"]])
         graph = gw.Graph.from_synth(g)
         q = c["q"].encode()
-        r = graph.align(q, c["vs"], c["ve"], max_lag=c["a_diff"])
+        ev = dict(evict_lag=c.get("evict_lag", 0), evict_every=c.get("evict_every", 0))
+        r = graph.align(q, c["vs"], c["ve"], max_lag=c["a_diff"], **ev)
         exp = dict(c["expect"])
         exp.setdefault("pruned", 0)
         assert_same(r, exp, c["name"])
+        assert r["evicted"] == exp.get("evicted", 0), c["name"]
         eng = gw.Engine(graph, prune=c["a_diff"] > 0)
         res = eng.align_batch(np.frombuffer(q, np.uint8), np.array([0, len(q)], np.uint64),
-                              [c["vs"]], [c["ve"]], max_lag=c["a_diff"])
+                              [c["vs"]], [c["ve"]], max_lag=c["a_diff"], **ev)
         assert_same(res[0], exp, c["name"] + "/batch")
+        assert int(res[0]["evicted"]) == exp.get("evicted", 0), c["name"]
 
 
 def test_config1_plain_one_launch_per_query():

@@ -59,3 +59,29 @@ def test_rejects_bad_arguments():
     g = synth.Graph.from_lists([b"ACGT"], [])
     assert oracle.gwfa(g, b"ACG", 0, 0, evict_lag=5, evict_every=1)["distance"] == -1          # needs pruning
     assert oracle.gwfa(g, b"ACG", 0, 0, a_diff=5, evict_lag=5, evict_every=0)["distance"] == -1
+
+
+PLANTED = ("GWFA_ORACLE_PLANT_EVICT_LE", "GWFA_ORACLE_PLANT_EVICT_OLDQ", "GWFA_ORACLE_PLANT_EVICT_BEFORE")
+
+
+@pytest.mark.parametrize("plant", PLANTED)
+def test_planted_eviction_mistakes_fail_the_hand_traces(plant, monkeypatch):
+    """The two hand-traced eviction cases (tests/golden/handtrace.json) pin the rule:
+    a planted mistake in the oracle -- keeping an entry that lags by exactly
+    evict_lag, keeping by the Q that GwfExtend left instead of the new Q, or evicting
+    before GwfExpand -- changes a traced counter on each of them (on the second, a
+    counter other than `evicted`: the spill no longer re-inserts the diagonal)."""
+    import json
+    import os
+    cases = [c for c in json.load(open(os.path.join(os.path.dirname(__file__), "golden", "handtrace.json")))["cases"]
+             if c.get("evict_lag")]
+    assert len(cases) >= 2
+    monkeypatch.setenv(plant, "1")
+    for c in cases:
+        g = synth.Graph.from_lists(c["labels"], [tuple(a) for a in c["arcs"]])
+        s = oracle.gwfa(g, c["q"].encode(), c["vs"], c["ve"], c["a_diff"], evict_lag=c["evict_lag"],
+                        evict_every=c["evict_every"])
+        changed = [k for k, v in c["expect"].items() if s[k] != v]
+        assert changed, (plant, c["name"])
+        if c["name"] == "evict_then_respill":
+            assert set(changed) - {"evicted"}, (plant, changed)

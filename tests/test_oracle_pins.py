@@ -206,7 +206,8 @@ def test_gwfa_handtraced_golden():
     cases = json.load(open(GOLDEN))["cases"]
     for c in cases:
         g = synth.Graph.from_lists(c["labels"], [tuple(a) for a in c["arcs"]])
-        s = oracle.gwfa(g, c["q"].encode(), c["vs"], c["ve"], c["a_diff"])
+        s = oracle.gwfa(g, c["q"].encode(), c["vs"], c["ve"], c["a_diff"],
+                        evict_lag=c.get("evict_lag", 0), evict_every=c.get("evict_every", 0))
         for k, v in c["expect"].items():
             assert s[k] == v, (c["name"], k, s[k], v)
         if c["a_diff"] == 0:
