@@ -128,8 +128,10 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_reference(args, g, qs, sample_s: float, cores: int | None = None):
-    """Time the oracle (Alg. 1-3 in C) on a bounded sample: one query per thread."""
+def cpu_reference(args, g, qs, sample_s: float, cores: int | None = None, keep: bool = False):
+    """Time the oracle (Alg. 1-3 in C) on a bounded sample: one query per thread.
+    With keep=True also return the sampled query ids and the oracle's results, so the
+    run can check the GPU's results against them."""
     import oracle
     oracle.build()
     cores = cores or os.cpu_count() or 1
@@ -139,17 +141,42 @@ def cpu_reference(args, g, qs, sample_s: float, cores: int | None = None):
     # grow the sample until it costs about `sample_s` seconds
     done, bases, t_total = 0, 0, 0.0
     chunk = max(cores * 8, 8)
+    got = []
     t0 = time.perf_counter()
     while done < len(order) and time.perf_counter() - t0 < sample_s:
         idx = order[done:done + chunk]
         ts = time.perf_counter()
-        oracle.gwfa_many(ga, qs, idx, threads=cores)
+        res = oracle.gwfa_many(ga, qs, idx, threads=cores)
         t_total += time.perf_counter() - ts
+        if keep:
+            got.extend(res)
         bases += int(qs.lengths()[idx].sum())
         done += len(idx)
-    return {"value": bases / t_total / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {len(qs)} queries ({bases} bp), random order, "
-                      f"{t_total:.1f} s wall on {cores} threads"}
+    out = {"value": bases / t_total / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{done} of {len(qs)} queries ({bases} bp), random order, "
+                     f"{t_total:.1f} s wall on {cores} threads"}
+    if keep:
+        return out, order[:done], got
+    return out
+
+
+VERIFY_FIELDS = (("edit_distance", "distance"), ("n_scores", "n_scores"), ("cells", "cells"),
+                 ("peak_frontier", "peak"), ("visited", "visited"), ("spills", "spills"))
+
+
+def verify(res, idx, want) -> dict:
+    """GPU results against the oracle's on the sampled queries: distance and work counters."""
+    bad = []
+    for i, w in zip(idx, want):
+        r = res[int(i)]
+        if w["distance"] < 0:
+            ok = int(r["status"]) == w["distance"]
+        else:
+            ok = int(r["status"]) == 0 and all(int(r[a]) == w[b] for a, b in VERIFY_FIELDS)
+        if not ok:
+            bad.append(int(i))
+    return {"verified_queries": len(want), "mismatches": len(bad), "mismatch_ids": bad[:20],
+            "fields": [a for a, _ in VERIFY_FIELDS]}
 
 
 def learned_schedule(gw, graph, qs, ref, stream, flush, args) -> dict:
@@ -259,19 +286,119 @@ def ncu_case(args):
                       "tier0_overflows": int((r1["status"] == gw.GWFA_ERR_CAPACITY).sum())}))
 
 
-def measured_traffic_per_cell():
-    """DRAM bytes per cell from the committed ncu summary, if it was taken on the
-    current kernel source (else None: the counters no longer describe this kernel)."""
+def kernel_counters():
+    """Per-cell counters of the alignment kernel from the committed ncu summary
+    (profiles/align_kernel_counters.json), if they were taken on the current kernel
+    source; else None: the counters no longer describe this kernel."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "align_kernel_traffic.json")
+    p = os.path.join(ROOT, "profiles", "align_kernel_counters.json")
     src = os.path.join(ROOT, "paper_2206_13574_gb300", "csrc", "gwfa_kernels.cu")
     if not os.path.exists(p):
-        return None, None
+        return None
     d = json.load(open(p))
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("kernel_source_sha256") != sha:
-        return None, d.get("source")
-    return float(d["dram_bytes_per_cell"]), d.get("source")
+    return d if d.get("kernel_source_sha256") == sha else None
+
+
+# Algorithmic bytes per cell (one live diagonal in one score) of the hot path, as the
+# work-unit analysis counts them: GwfExtend reads the diagonal (12 B), one window of
+# the query and of the label (8 B) and the vertex record (8 B) and writes the offset
+# (4 B); GwfExpand makes up to 3 candidate merges and 2 probes of the old H~ (16 B
+# each) and writes up to 3 frontier entries (12 B each) -- about 120 B -- plus 0.5 B
+# per aligned base (2 bits of query and label each).
+B_CELL = 120
+# The kernel's own minimum (its design keeps the diagonal, the vertex record and the
+# windows in registers and L1 and merges the frontier per 8-diagonal tile): the offset
+# read and written by GwfExtend (8 B), the snapshot read and up to three candidates
+# written by GwfExpand (16 B).
+B_CELL_KERNEL = 24
+
+
+def roofline(cells: int, aligned_bp: int, t_kernel: float, int_peak: dict | None, counters: dict | None,
+             peak_gbs: float, peak_kind: str, steps: int) -> dict:
+    alg = B_CELL * cells + 0.5 * aligned_bp
+    achieved = alg / t_kernel / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+           "frac": achieved / peak_gbs, "hbm_frac": achieved / peak_gbs,
+           "traffic": None, "peak_kind": f"{peak_kind} HBM copy",
+           "kernel": "align_kernel<exact> (all tiers of one step; CUDA events on its stream)",
+           "bytes_per_cell": B_CELL, "bytes_per_aligned_base": 0.5,
+           "kernel_bytes_per_cell": B_CELL_KERNEL,
+           "hbm_frac_kernel_bytes": (B_CELL_KERNEL * cells + 0.5 * aligned_bp) / t_kernel / 1e9 / peak_gbs,
+           "int_frac": None, "l2_frac": None}
+    if counters:
+        out["traffic"] = counters["dram_bytes_per_cell"] * cells
+        out["traffic_note"] = ("ncu dram read+write per cell on the profiling case, scaled to this "
+                               "step's cells: " + counters.get("source", ""))
+        out["dram_bytes_per_cell_measured"] = counters["dram_bytes_per_cell"]
+        out["l2_frac"] = counters["l2_throughput_pct"] / 100.0
+        out["l2_note"] = "ncu lts__throughput (% of peak) of the profiled launch"
+        out["warp_inst_per_cell"] = counters["warp_inst_per_cell"]
+        out["alu_warp_inst_per_cell"] = counters["alu_warp_inst_per_cell"]
+        if int_peak:
+            rate = counters["alu_warp_inst_per_cell"] * cells / t_kernel
+            out["int_achieved_warp_inst_per_s"] = rate
+            out["int_peak_warp_inst_per_s"] = int_peak["warp_inst_per_s"]
+            out["int_frac"] = rate / int_peak["warp_inst_per_s"]
+            out["int_note"] = ("ALU-pipe warp instructions per cell (ncu) x cells / kernel time, against "
+                               "the lop3 microbenchmark's ALU-pipe rate measured in this run")
+    else:
+        out["traffic_note"] = "no ncu counters for the current kernel source"
+    if int_peak:
+        out["int_peak"] = int_peak
+    return out
+
+
+def leg_config3() -> dict:
+    """Cyclic graph with tandem-repeat loops, 2,000 x 50 kb at 8% errors: lag-pruned
+    (a_diff 1000, all queries) against exact (200 queries), with the exact-match rate."""
+    from paper_2206_13574_gb300 import experiments
+    t0 = time.perf_counter()
+    r = experiments.config3(n_pruned=2000, n_exact=200, a_diff=1000)
+    r["leg_wall_s"] = time.perf_counter() - t0
+    return r
+
+
+def leg_config4(n: int) -> dict:
+    """50 Mb graph, n lognormal 1-100 kb queries at 0.1-10% divergence, exact: the plain
+    longest-first scheduler against the learned plan (cost model trained on config-2
+    and config-3-graph logs)."""
+    from paper_2206_13574_gb300 import experiments
+    t0 = time.perf_counter()
+    r = experiments.scheduler(n=n, n_plain=0, only=("plain_longest_first", "learned"))
+    r["learned_vs_longest_first"] = r["plain_longest_first"]["s"] / r["learned"]["s"]
+    r["leg_wall_s"] = time.perf_counter() - t0
+    return r
+
+
+def leg_config5(rates=(1000.0, 2000.0, 5000.0, 10000.0, 20000.0, 50000.0), max_requests: int = 4000,
+                duration: float = 2.0) -> dict:
+    """The 50 Mb graph resident in the continuous-batching server, Poisson arrivals at
+    rising rates until the server saturates (throughput below 80% of the offered rate)."""
+    import paper_2206_13574_gb300 as gw
+    from paper_2206_13574_gb300 import serving as sv
+    from paper_2206_13574_gb300 import synth
+    t0 = time.perf_counter()
+    g, qs = synth.make_config(5, n_queries=3000)
+    graph = gw.Graph.from_synth(g)
+    srv = gw.Server(graph)
+    out = {"workload": "config5: 50 Mb graph resident, lognormal 1-100 kb queries, 0.1-10% divergence, "
+                       "Poisson arrivals", "sweep": []}
+    for lam in rates:
+        arr = synth.poisson_arrivals(lam, min(duration, max_requests / lam), seed=int(lam))
+        idx = np.arange(len(arr)) % len(qs)
+        summ, _ = sv.run_server(srv, qs, arr, idx)
+        summ["lambda"] = lam
+        out["sweep"].append(summ)
+        if summ["throughput_qps"] < 0.8 * lam:
+            out["saturated_at_lambda"] = lam
+            break
+    out["max_throughput_qps"] = max(x["throughput_qps"] for x in out["sweep"])
+    out["server"] = srv.stats()
+    srv.close()
+    graph.close()
+    out["leg_wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def main():
@@ -284,10 +411,14 @@ def main():
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-wide", type=int, default=0, help="queries on the wide CTA class")
-    ap.add_argument("--no-extras", action="store_true", help="skip plain / learned / serving legs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain / learned / serving legs and the config 3-5 legs")
+    ap.add_argument("--legs", default="3,4,5", help="config legs beside the headline (comma list, '' = none)")
+    ap.add_argument("--c4-queries", type=int, default=5000)
     ap.add_argument("--plain-sample", type=int, default=300)
     ap.add_argument("--ncu-case", action="store_true",
                     help="small profiling case: --queries (default 2000) on ~3 GB of slabs, two batches")
+    ap.add_argument("--int-peak-only", action="store_true", help="run the integer microbenchmark and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -295,6 +426,12 @@ def main():
     from paper_2206_13574_gb300 import synth
     if args.ncu_case:
         return ncu_case(args)
+    if args.int_peak_only:
+        import paper_2206_13574_gb300 as gw
+        from paper_2206_13574_gb300 import _build
+        _build.build()
+        print(json.dumps(gw.measure_int_peak(local)))
+        return
     g, qs = synth.make_config(2, n_queries=args.queries)
     total_bp = int(qs.lengths().sum())
 
@@ -352,9 +489,8 @@ def main():
         step()
     torch.cuda.synchronize()
     res = batch.results()
-    ok = res["status"] == 0
-    aligned_bp = int(qs.lengths()[ok].sum())
     launches_per_step = eng.last_launches
+    int_peak = gw.measure_int_peak(local)   # integer ceiling of this GPU, this run
 
     clocks = ClockSampler(local)
     if ws > 1:
@@ -377,6 +513,8 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     t_step = float(np.mean(times))
+    res_t = batch.results()
+    assert np.array_equal(res_t["edit_distance"], res["edit_distance"])
 
     # end to end through the host-buffer entry point, inputs in pinned host memory
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -413,19 +551,28 @@ def main():
     h2d = int(qs.seq.nbytes + qs.off.nbytes + qs.v_s.nbytes + qs.v_e.nbytes + order.nbytes)
     d2h = len(qs) * gw.RESULT_DTYPE.itemsize
 
+    # bit-exactness checked in this run: the oracle's results on the CPU-baseline
+    # sample against the GPU's, distance and work counters
+    cpu, check = None, {"verified_queries": 0, "mismatches": 0,
+                        "note": "no oracle sample in this run (--no-cpu-baseline or rank > 0)"}
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, vidx, vres = cpu_reference(args, g, qs, sample_s=args.cpu_sample_s, keep=True)
+        check = verify(res, vidx, vres)
+        one = cpu_reference(args, g, qs, sample_s=max(2.0, args.cpu_sample_s / 4), cores=1)
+        cpu["single_core"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
+    ok = res["status"] == 0
+    if check["mismatches"]:
+        # an unverified batch: only the sampled queries that matched the oracle count
+        good = np.zeros(len(qs), dtype=bool)
+        good[np.setdiff1d(vidx, check["mismatch_ids"])] = True
+        ok = ok & good
+    aligned_bp = int(qs.lengths()[ok].sum())
     cells = int(res["cells"][ok].sum())
     # every rank's units and the slowest rank's times make the whole-job figures
     t_step, t_e2e, job_bp, job_cells = reduce_ranks(t_step, t_e2e, aligned_bp, cells, dev)
     value = job_bp / t_step / 1e9
-    # algorithmic bytes of the hot path: per live diagonal and score, the offset is
-    # read and written by GwfExtend (8 B) and read again plus up to three candidate
-    # offsets written by GwfExpand (16 B); every aligned base is read once from the
-    # packed query and once from the packed graph (2 bits each).
-    B_CELL = 24
-    alg_bytes = B_CELL * cells + 0.5 * aligned_bp
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / t_step / 1e9
-    tpc, tsrc = measured_traffic_per_cell()
+    roof = roofline(cells, aligned_bp, t_step, int_peak, kernel_counters(), peak, peak_kind, args.steps)
 
     # S4: the plain path (one launch per query, synchronous) on a random sample
     plain = None
@@ -451,11 +598,16 @@ def main():
     if not args.no_extras:
         serving_out = serving_run(gw, graph, qs, res)
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_reference(args, g, qs, sample_s=args.cpu_sample_s)
-        one = cpu_reference(args, g, qs, sample_s=max(2.0, args.cpu_sample_s / 4), cores=1)
-        cpu["single_core"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
+    eng.close()
+    legs = {}
+    if not args.no_extras and rank == 0:
+        want = [x for x in args.legs.split(",") if x.strip()]
+        if "3" in want:
+            legs["config3"] = leg_config3()
+        if "4" in want:
+            legs["config4_scheduling"] = leg_config4(args.c4_queries)
+        if "5" in want:
+            legs["config5_serving"] = leg_config5()
 
     if rank == 0:
         line = {
@@ -474,19 +626,12 @@ def main():
                             eng.config.tiers[t].threads or eng.config.threads]
                            for t in range(eng.config.n_tiers)],
                        "threads_per_cta": eng.config.threads,
-                       "ok_queries": int(ok.sum())},
+                       "ok_queries": int((res["status"] == 0).sum())},
+            "verification": check,
             "e2e": {"value": job_bp / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e * 1e3},
             "gpu_launches": launches_per_step * args.steps * ws,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": (tpc * cells) if tpc is not None else None,
-                         "traffic_note": ("ncu dram read+write per cell on a 2,000-query case, scaled to "
-                                          f"this step's cells ({tsrc})") if tpc is not None else
-                                         "no ncu counters for the current kernel source",
-                         "peak_kind": f"{peak_kind} HBM copy",
-                         "kernel": "align_kernel<exact> (all tiers of one step)",
-                         "bytes_per_cell": B_CELL},
+            "roofline": roof,
             "cells_per_s": job_cells / t_step,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -495,6 +640,7 @@ def main():
             "learned_schedule": learned,
             "serving": serving_out,
         }
+        line.update(legs)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

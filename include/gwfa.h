@@ -271,19 +271,26 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n_queries, const uint32_t *
  * floor((32 MiB - 256 B) / slab) CTA slabs of 2^log2_tiles hash tiles each
  * (log2_tiles 0 = 15: five CTAs in exact mode, three with pruning).  There is
  * no overflow tier: a query needing more than 3/4 of its slab gets status
- * GWFA_ERR_CAPACITY.  A log2_tiles whose slab does not fit the array is rejected
- * with GWFA_ERR_CAPACITY before any GPU work.  Inputs and outputs are the
- * caller's device buffers, laid out as for gwfa_align_batch_device (d_words
- * from gwfa_pack_queries_device); the call only enqueues work on `stream`
- * (NULL = the legacy default stream) and calls no allocation routine.
+ * GWFA_ERR_CAPACITY.  log2_tiles outside [8, 24] (other than 0) is
+ * GWFA_ERR_INVALID; a valid log2_tiles whose slab does not fit the array is
+ * rejected with GWFA_ERR_CAPACITY, both before any GPU work.  Inputs and outputs
+ * are the caller's device buffers, laid out as for gwfa_align_batch_device
+ * (d_words from gwfa_pack_queries_device); d_status may be NULL, else it is the
+ * status array that packing wrote, and a query with a nonzero status (a base
+ * other than A/C/G/T) is not aligned and keeps that status in d_out, as in
+ * gwfa_align_batch_device.  With d_status NULL such a query is aligned with its
+ * bad bases read as A.  The call only enqueues work on `stream` (NULL = the
+ * legacy default stream) and calls no allocation routine.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call shares
- * the array and resets it first, so calls whose GPU work overlaps race on it:
- * the caller must serialise them (one stream, or its own ordering).
+ * device, and again if a device reset replaced the context); make that first
+ * call before any stream capture.  Every call shares the array and resets it
+ * first, so calls whose GPU work overlaps race on it: the caller must serialise
+ * them (one stream, or its own ordering).
  */
 int gwfa_align_noalloc(const gwfa_graph *g, uint32_t n_queries, const uint32_t *d_words,
                        const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
-                       uint32_t log2_tiles, const gwfa_opts *opts, gwfa_result *d_out, void *stream);
+                       const int32_t *d_status, uint32_t log2_tiles, const gwfa_opts *opts,
+                       gwfa_result *d_out, void *stream);
 
 /* Walk output of later batch calls with opts.traceback = 1: query i writes its
  * walk to d_paths[i * path_cap ...] (at most path_cap ids) and its full length to
@@ -401,6 +408,11 @@ int gwfa_model_get_params(const gwfa_model *m, float *h_params, uint32_t n_param
 /* feature means/stds (GWFA_MODEL_FEATURES each) and target means/stds (GWFA_MODEL_TARGETS) */
 int gwfa_model_set_normalization(gwfa_model *m, const float *h_fmean, const float *h_fstd,
                                  const float *h_tmean, const float *h_tstd);
+/* write the weights and the normalisation to a file at `path` / read them back
+ * (the parameter and normalisation shapes are checked); GWFA_ERR_INVALID for a file
+ * that cannot be opened, written or parsed.  Both synchronise the model's device. */
+int gwfa_model_save(const gwfa_model *m, const char *path);
+int gwfa_model_load(gwfa_model *m, const char *path);
 /* raw features of n packed queries (layout of gwfa_pack_queries_device) into d_feat[n][6] */
 int gwfa_model_features_device(gwfa_model *m, uint32_t n, const uint32_t *d_words,
                                const uint64_t *d_q_off, const uint32_t *d_v_s, const uint32_t *d_v_e,
@@ -486,6 +498,21 @@ int gwfa_wait(gwfa_server *s, uint64_t ticket, uint32_t timeout_ms, gwfa_result 
 int gwfa_server_get_stats(gwfa_server *s, gwfa_server_stats *out);
 /* stops the kernel (requests on the GPU finish first) and frees everything */
 int gwfa_server_destroy(gwfa_server *s);
+
+/* ---- measurement -------------------------------------------------------- */
+/*
+ * Integer-pipe ceiling of `device` (used to report the alignment kernels against
+ * their roofline; the paper has no counterpart -- its complexity analysis, Sec. 2.4,
+ * bounds the work, not the machine).  Runs a kernel of blocks_per_sm (0 = 2)
+ * 1024-thread CTAs per SM in which every thread issues `iters` x 64 independent
+ * 3-input logic operations (lop3, ALU pipe, no memory traffic), four times on a
+ * private stream; *ms_out = the fastest of the last three runs (CUDA events) and
+ * *warp_insts_out = the lop3 warp instructions one run issues.  Their ratio is the
+ * ALU-pipe warp-instruction rate of the whole GPU.  Synchronous; allocates nothing
+ * but a stream and two events.  GWFA_ERR_INVALID for NULL outputs or iters = 0.
+ */
+int gwfa_measure_int_peak(int device, uint32_t blocks_per_sm, uint32_t iters, float *ms_out,
+                          uint64_t *warp_insts_out);
 
 #ifdef __cplusplus
 }

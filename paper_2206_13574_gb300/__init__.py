@@ -144,7 +144,11 @@ class gwfa_server_stats(ctypes.Structure):
 
 
 SIGNATURES.update({
-    "gwfa_align_noalloc": ([_P, _u32, _P, _P, _P, _P, _u32, ctypes.POINTER(gwfa_opts), _P, _P],
+    "gwfa_model_save": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "gwfa_model_load": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "gwfa_measure_int_peak": ([ctypes.c_int, _u32, _u32, ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "gwfa_align_noalloc": ([_P, _u32, _P, _P, _P, _P, _P, _u32, ctypes.POINTER(gwfa_opts), _P, _P],
                            ctypes.c_int),
     "gwfa_align_path": ([_P, _P, _u32, _u32, _u32, ctypes.POINTER(gwfa_opts), ctypes.POINTER(gwfa_result),
                          _P, _u32, ctypes.POINTER(_u32)], ctypes.c_int),
@@ -457,6 +461,20 @@ class CostModel:
                "gwfa_model_train_device")
         return losses
 
+    def save(self, path: str):
+        """Weights and normalisation to a file (gwfa_model_save)."""
+        _check(load().gwfa_model_save(self.handle, os.fsencode(path)), "gwfa_model_save")
+
+    def load(self, path: str):
+        """Weights and normalisation from a file written by save (gwfa_model_load)."""
+        _check(load().gwfa_model_load(self.handle, os.fsencode(path)), "gwfa_model_load")
+        # the file's normalisation block follows the tag, three counts and the weights
+        raw = np.fromfile(path, dtype=np.float32, offset=8 + 12 + 4 * MODEL_PARAMS)
+        nf, nt = MODEL_FEATURES, MODEL_TARGETS
+        cuts = np.cumsum([nf, nf, nt, nt])
+        self.norm = [raw[0:cuts[0]].copy(), raw[cuts[0]:cuts[1]].copy(), raw[cuts[1]:cuts[2]].copy(),
+                     raw[cuts[2]:cuts[3]].copy()]
+
     @property
     def params(self) -> np.ndarray:
         w = np.zeros(MODEL_PARAMS, dtype=np.float32)
@@ -616,5 +634,18 @@ def align_noalloc(graph: Graph, batch: "DeviceBatch", log2_tiles: int = 0, max_l
     st = stream if stream is not None else torch.cuda.current_stream(batch.q.device)
     o = _opts(max_lag, max_score)
     return int(load().gwfa_align_noalloc(graph.handle, batch.n, batch.words.data_ptr(), batch.q_off.data_ptr(),
-                                         batch.v_s.data_ptr(), batch.v_e.data_ptr(), log2_tiles,
+                                         batch.v_s.data_ptr(), batch.v_e.data_ptr(), batch.status.data_ptr(),
+                                         log2_tiles,
                                          ctypes.byref(o), batch.out.data_ptr(), st.cuda_stream or None))
+
+
+def measure_int_peak(device: int = 0, iters: int = 20000, blocks_per_sm: int = 2) -> dict:
+    """ALU-pipe ceiling of the GPU from the library's lop3 microbenchmark
+    (gwfa_measure_int_peak): warp instructions per second, and per SM per cycle at
+    the SM clock the caller reports."""
+    ms = ctypes.c_float()
+    n = ctypes.c_uint64()
+    _check(load().gwfa_measure_int_peak(device, blocks_per_sm, iters, ctypes.byref(ms), ctypes.byref(n)),
+           "gwfa_measure_int_peak")
+    return {"warp_insts": int(n.value), "ms": float(ms.value),
+            "warp_inst_per_s": int(n.value) / (float(ms.value) * 1e-3)}

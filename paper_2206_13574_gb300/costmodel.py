@@ -68,14 +68,13 @@ def transfer(src: CostModel, dst: CostModel):
 
 
 def save(model: CostModel, path: str):
-    np.savez(path, params=model.params, fmean=model.norm[0], fstd=model.norm[1],
-             tmean=model.norm[2], tstd=model.norm[3])
+    """Weights and normalisation to `path` (the library's gwfa_model_save format)."""
+    model.save(path)
 
 
 def load_into(model: CostModel, path: str):
-    z = np.load(path)
-    model.params = z["params"]
-    model.set_normalization(z["fmean"], z["fstd"], z["tmean"], z["tstd"])
+    """Weights and normalisation from a file written by save (gwfa_model_load)."""
+    model.load(path)
 
 
 def capacities(config) -> tuple[int, int]:

@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -396,6 +397,47 @@ int gwfa_model_set_normalization(gwfa_model *m, const float *fmean, const float 
     memcpy(m->norm.tmean, tmean, sizeof(m->norm.tmean));
     memcpy(m->norm.tstd, tstd, sizeof(m->norm.tstd));
     return GWFA_OK;
+}
+
+// Model file: 8-byte tag, the parameter / feature / target counts (uint32 each), then
+// the fp32 parameters and the four normalisation vectors, host byte order.
+static const char kModelTag[8] = {'G', 'W', 'F', 'A', 'M', 'L', 'P', '1'};
+
+int gwfa_model_save(const gwfa_model *m, const char *path) {
+    if (!m || !path) return GWFA_ERR_INVALID;
+    std::vector<float> w(NPARAM);
+    int st = gwfa_model_get_params(m, w.data(), NPARAM);
+    if (st) return st;
+    Norm nm;
+    {
+        std::lock_guard<std::mutex> lk(const_cast<gwfa_model *>(m)->mu);
+        nm = m->norm;
+    }
+    FILE *f = fopen(path, "wb");
+    if (!f) return GWFA_ERR_INVALID;
+    const uint32_t dims[3] = {(uint32_t)NPARAM, (uint32_t)F, (uint32_t)O};
+    bool ok = fwrite(kModelTag, 1, 8, f) == 8 && fwrite(dims, 4, 3, f) == 3 &&
+              fwrite(w.data(), 4, NPARAM, f) == (size_t)NPARAM && fwrite(&nm, sizeof(nm), 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? GWFA_OK : GWFA_ERR_INVALID;
+}
+
+int gwfa_model_load(gwfa_model *m, const char *path) {
+    if (!m || !path) return GWFA_ERR_INVALID;
+    FILE *f = fopen(path, "rb");
+    if (!f) return GWFA_ERR_INVALID;
+    char tag[8];
+    uint32_t dims[3];
+    std::vector<float> w(NPARAM);
+    Norm nm;
+    bool ok = fread(tag, 1, 8, f) == 8 && memcmp(tag, kModelTag, 8) == 0 && fread(dims, 4, 3, f) == 3 &&
+              dims[0] == (uint32_t)NPARAM && dims[1] == (uint32_t)F && dims[2] == (uint32_t)O &&
+              fread(w.data(), 4, NPARAM, f) == (size_t)NPARAM && fread(&nm, sizeof(nm), 1, f) == 1;
+    fclose(f);
+    if (!ok) return GWFA_ERR_INVALID;
+    int st = gwfa_model_set_normalization(m, nm.fmean, nm.fstd, nm.tmean, nm.tstd);
+    if (!st) st = gwfa_model_set_params(m, w.data(), NPARAM);
+    return st;
 }
 
 int gwfa_model_features_device(gwfa_model *m, uint32_t n, const uint32_t *d_words,

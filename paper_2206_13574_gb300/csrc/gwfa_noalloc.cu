@@ -15,6 +15,7 @@
 // re-initialises it (work-queue counter to zero, hash slabs to empty) before its
 // kernel, so calls whose GPU work overlaps (two streams, or two host threads)
 // race on it and must be serialised by the caller.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,13 +33,47 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocScratchBytes]
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context the address belongs to
 
-// Device address of g_noalloc_scratch on the current device, looked up once per
-// device (the host-side name of the array is not a device address).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Identifier of the calling thread's current context (unique for the life of the
+// process, so a device reset that replaces the primary context changes it); 0 if
+// the driver cannot tell.  The driver functions are found through the runtime, so
+// the library does not link the driver library itself.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch on the current device (the host-side name of
+// the array is only a stand-in, not a device address).  Looked up once per device
+// and context: the first call on a device does it, and again after a device reset
+// has replaced the context the cached address belonged to.
 int scratch_address(int dev, uint8_t **out) {
     if (dev < 0 || dev >= kMaxDevices) return GWFA_ERR_INVALID;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -46,6 +81,7 @@ int scratch_address(int dev, uint8_t **out) {
             return GWFA_ERR_CUDA;
         }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = (uint8_t *)g_scratch_addr[dev];
     return GWFA_OK;
@@ -55,14 +91,14 @@ int scratch_address(int dev, uint8_t **out) {
 
 extern "C" int gwfa_align_noalloc(const gwfa_graph *g, uint32_t n_queries, const uint32_t *d_words,
                                   const uint64_t *d_q_off, const uint32_t *d_v_s,
-                                  const uint32_t *d_v_e, uint32_t log2_tiles, const gwfa_opts *opts,
-                                  gwfa_result *d_out, void *stream) {
+                                  const uint32_t *d_v_e, const int32_t *d_status, uint32_t log2_tiles,
+                                  const gwfa_opts *opts, gwfa_result *d_out, void *stream) {
     if (!g || !d_words || !d_q_off || !d_v_s || !d_v_e || !d_out) return GWFA_ERR_INVALID;
     const gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
     if (o.max_lag < 0 || o.traceback != 0 || o.ends != 0 || o.evict_lag != 0) return GWFA_ERR_INVALID;
     if (log2_tiles == 0) log2_tiles = 15;
     const bool prune = o.max_lag > 0;
-    if (log2_tiles < 8 || log2_tiles > gwfa::kMaxLog2Tiles) return GWFA_ERR_CAPACITY;
+    if (log2_tiles < 8 || log2_tiles > gwfa::kMaxLog2Tiles) return GWFA_ERR_INVALID;
     const uint64_t slab = gwfa::slab_layout(log2_tiles, prune).total;
     if (slab + kHeadBytes > kNoallocScratchBytes) return GWFA_ERR_CAPACITY;   // does not fit the array
     if (n_queries == 0) return GWFA_OK;
@@ -82,6 +118,7 @@ extern "C" int gwfa_align_noalloc(const gwfa_graph *g, uint32_t n_queries, const
     a.q_off = d_q_off;
     a.v_s = d_v_s;
     a.v_e = d_v_e;
+    a.qstatus = d_status;   // a query the packing rejected keeps its status
     a.out = d_out;
     a.count_val = n_queries;
     a.head = (uint32_t *)base;

@@ -1,5 +1,7 @@
 """Learned cost model: CPU pins of the fp64 reference and the planner; GPU parity of
 the feature, gradient and training kernels; the gain of the learned schedule."""
+import os
+
 import numpy as np
 import pytest
 
@@ -144,6 +146,19 @@ def test_training_learns_work_counts(c2small):
     pred = m.predict(tf).cpu().numpy()
     r2 = costmodel.r2(pred, tt.cpu().numpy())
     assert r2[0] > 0.6 and r2[3] > 0.6, r2         # distance and work on held-out queries
+    # the trained model through a file (gwfa_model_save / gwfa_model_load) predicts the same
+    import tempfile
+    path = os.path.join(tempfile.mkdtemp(), "model.bin")
+    m.save(path)
+    m2 = gw.CostModel(graph, seed=99)
+    m2.load(path)
+    assert np.array_equal(m2.params, m.params)
+    assert all(np.array_equal(a, b) for a, b in zip(m2.norm, m.norm))
+    assert np.array_equal(m2.predict(tf).cpu().numpy(), pred)
+    with open(path, "r+b") as f:   # a damaged tag is refused
+        f.write(b"X")
+    with pytest.raises(gw.GwfaError):
+        m2.load(path)
 
 
 @pytest.mark.gpu
