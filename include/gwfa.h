@@ -55,9 +55,9 @@ const char *gwfa_strerror(int status);
 /* ---- options and results ------------------------------------------------ */
 typedef struct {
     int32_t max_lag;     /* a_diff of Alg. 4 (Sec. 2.5); 0 = exact (no pruning) */
-    int32_t traceback;   /* 1: record the alignment walk (Alg. 5-6); needs max_lag == 0 and
-                            64-bit slabs (engine prune_slabs); see gwfa_align_path /
-                            gwfa_engine_set_paths */
+    int32_t traceback;   /* 1: record the alignment walk (Alg. 5-6), with or without
+                            pruning; needs 64-bit slabs (engine prune_slabs) and no
+                            evict_lag; see gwfa_align_path / gwfa_engine_set_paths */
     int32_t max_score;   /* stop with GWFA_ERR_SCORE_LIMIT once d would exceed it; -1 = no limit */
     int32_t wait_limit;  /* serving: iteration limit of device-side waits; 0 = default */
     int32_t ends;        /* formulation variant (Sec. 2.1), GWFA_FREE_* / GWFA_EXTEND flags;
@@ -157,7 +157,10 @@ int gwfa_align(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t v_s, u
  * whose spelled sequence is at edit distance out->edit_distance from the query
  * (several optimal walks may exist; this returns one).  h_path[path_cap] gets
  * the first min(path_cap, *path_len) vertex ids; *path_len is the full length.
- * opts->max_lag must be 0 (traceback with pruning is not supported).
+ * With pruning (opts->max_lag > 0) the walk is the one the pruned wavefront
+ * reached the end cell along: the query aligns to its spelled sequence with at
+ * most out->edit_distance edits (the upper bound), and with at least the exact
+ * distance.
  */
 int gwfa_align_path(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t v_s, uint32_t v_e,
                     const gwfa_opts *opts, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
@@ -180,7 +183,7 @@ typedef struct gwfa_engine gwfa_engine;
  *                  n_wide queries of the schedule (gwfa_schedule), so the heaviest
  *                  queries start at once on slabs that fit them instead of forming a
  *                  tail of overflow re-runs; their overflows go to the retry tiers
- *   threads        threads per CTA (multiple of 32, 64..1024; above 512 a CTA
+ *   threads        threads per CTA (multiple of 32, 32..1024; above 512 a CTA
  *                  takes half an SM: for the few heaviest queries, e.g. the huge
  *                  class, whose own latency bounds a batch); 0 = 128
  *   max_queries, max_bases  sizes of the engine's staging buffers for the

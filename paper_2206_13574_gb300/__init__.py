@@ -251,10 +251,11 @@ class Graph:
         return r.as_dict()
 
     def align_path(self, q: bytes, v_s: int, v_e: int, max_score: int = -1, path_cap: int = 1 << 16,
-                   ends: int = 0):
-        """(result, walk) with the optimal walk's vertex ids (gwfa_align_path)."""
+                   ends: int = 0, max_lag: int = 0):
+        """(result, walk) with the optimal walk's vertex ids (gwfa_align_path); with
+        max_lag > 0 the walk the lag-pruned wavefront reached the end along."""
         r = gwfa_result()
-        o = _opts(0, max_score, 0, ends)
+        o = _opts(max_lag, max_score, 0, ends)
         qb = bytes(q)
         path = np.zeros(path_cap, dtype=np.uint32)
         plen = _u32()

@@ -236,7 +236,7 @@ int gwfa_align_path(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_t v
                     const gwfa_opts *opts, gwfa_result *out, uint32_t *h_path, uint32_t path_cap,
                     uint32_t *path_len) {
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag != 0 || !path_len || (path_cap && !h_path)) return GWFA_ERR_INVALID;
+    if (!path_len || (path_cap && !h_path)) return GWFA_ERR_INVALID;
     o.traceback = 1;
     return align_plain(g, h_q, n, vs, ve, o, out, h_path, path_cap, path_len);
 }
@@ -250,8 +250,7 @@ static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_
     out->edit_distance = -1;
     if (path_len) *path_len = 0;
     if (o.ends & GWFA_EXTEND) ve = vs;   // no end vertex
-    if (vs >= g->nv || ve >= g->nv || o.max_lag < 0 || n >= 0x7FFFFFFFu ||
-        (o.traceback && o.max_lag != 0) || !ends_ok(o)) {
+    if (vs >= g->nv || ve >= g->nv || o.max_lag < 0 || n >= 0x7FFFFFFFu || !ends_ok(o)) {
         out->status = GWFA_ERR_INVALID;
         return GWFA_ERR_INVALID;
     }
@@ -262,7 +261,7 @@ static int align_plain(const gwfa_graph *g, const char *h_q, uint32_t n, uint32_
     std::lock_guard<std::mutex> lk(g->mu);
     int st = cuda_status(cudaSetDevice(g->device));
     if (st) return st;
-    const bool prune = o.max_lag > 0 || o.traceback;   // 64-bit values (base or trace payload)
+    const bool prune = o.max_lag > 0 || o.traceback;   // 64-bit values (walk base) and trace words
     // staging: query bytes | q_off[2] | v_s | v_e | words | status | head | result | path
     const uint64_t need = gwfa::align256(n + 16) + 256 * 6 + gwfa::align256(words_for(1, n) * 4) +
                           gwfa::align256(sizeof(gwfa_result)) + gwfa::align256((uint64_t)path_cap * 4) + 1024;
@@ -407,13 +406,13 @@ int gwfa_engine_create(const gwfa_graph *g, const gwfa_engine_config *cfg, gwfa_
     *out = nullptr;
     if (cfg->n_tiers < 1 || cfg->n_tiers > GWFA_MAX_TIERS) return GWFA_ERR_INVALID;
     const uint32_t threads = cfg->threads ? cfg->threads : 128;
-    if (threads % 32 || threads < 64 || threads > 1024) return GWFA_ERR_INVALID;
+    if (threads % 32 || threads < 32 || threads > 1024) return GWFA_ERR_INVALID;
     for (uint32_t t = 0; t < cfg->n_tiers + 2; ++t) {
         const gwfa_tier &tt = t < cfg->n_tiers ? cfg->tiers[t] : (t == cfg->n_tiers ? cfg->wide : cfg->huge);
         if (t >= cfg->n_tiers && tt.ctas == 0) continue;   // class not used
         const uint32_t th = tt.threads;
         if (tt.ctas == 0 || tt.log2_tiles < 8 || tt.log2_tiles > gwfa::kMaxLog2Tiles ||
-            (th && (th % 32 || th < 64 || th > 1024)))
+            (th && (th % 32 || th < 32 || th > 1024)))
             return GWFA_ERR_INVALID;
     }
     int st = cuda_status(cudaSetDevice(g->device));
@@ -672,7 +671,7 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n, const uint32_t *d_words,
     gwfa::Range range_("gwfa_align_batch_device");
     if (!e || !d_words || !d_q_off || !d_vs || !d_ve || !d_out) return GWFA_ERR_INVALID;
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0) || !ends_ok(o)) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || !ends_ok(o)) return GWFA_ERR_INVALID;
     if ((o.max_lag > 0 || o.traceback) && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
     if (n == 0) return GWFA_OK;
     std::lock_guard<std::mutex> lk(e->mu);
@@ -690,7 +689,7 @@ int gwfa_align_batch(gwfa_engine *e, uint32_t n, const char *h_q, const uint64_t
     if (!e || !h_q_off || !h_vs || !h_ve || !h_out) return GWFA_ERR_INVALID;
     gwfa::Range range_("gwfa_align_batch");
     gwfa_opts o = opts ? *opts : gwfa_opts{0, 0, -1, 0};
-    if (o.max_lag < 0 || (o.traceback && o.max_lag != 0) || !ends_ok(o)) return GWFA_ERR_INVALID;
+    if (o.max_lag < 0 || !ends_ok(o)) return GWFA_ERR_INVALID;
     if ((o.max_lag > 0 || o.traceback) && !e->cfg.prune_slabs) return GWFA_ERR_INVALID;
     if (n == 0) return GWFA_OK;
     if (h_q_off[0] != 0) return GWFA_ERR_INVALID;

@@ -57,23 +57,27 @@ constexpr uint32_t kMaxLog2Tiles = 24;   // slot must fit the 24 low bits of EHd
 
 // Hash slot of one tile, one 64-byte line in exact mode (128 in pruning mode):
 // key (v << 32 | kb, all ones = empty), the two lane-mask words of the phase
-// parities, and the 8 offsets.  A tile visit touches a single line.
+// parities, and the 8 offsets; in pruning mode also the 8 trace indices (Alg. 5)
+// of the diagonals, used with traceback.  A tile visit touches a single line.
 template <class T>
 struct alignas(sizeof(T) == 4 ? 64 : 128) SlotT {
     unsigned long long key;
     uint32_t reg[2];
     T vals[kTile];
+    uint32_t trace[sizeof(T) == 4 ? 1 : kTile];
 };
-// Extended-frontier entry: header + snapshot of the 8 offsets after extension.
+// Extended-frontier entry: header + snapshot of the 8 offsets (and, in pruning
+// mode, of their trace indices) after extension.
 template <class T>
 struct alignas(sizeof(T) == 4 ? 64 : 128) EEntT {
     EHdr hdr;
     T vals[kTile];
+    uint32_t trace[sizeof(T) == 4 ? 1 : kTile];
 };
 
 // Per-CTA slab layout (all arrays 256-byte aligned), cap = 2^log2 tiles.
 struct SlabLayout {
-    uint64_t slots, touched, qlist, slist0, slist1, elist, req, trace, total, slot_bytes;
+    uint64_t slots, touched, qlist, slist0, slist1, elist, req, reqt, trace, total, slot_bytes;
 };
 
 __host__ __device__ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -92,6 +96,7 @@ __host__ __device__ inline SlabLayout slab_layout(uint32_t log2cap, bool prune) 
     L.slist1 = o;  o = align256(o + cap * sizeof(LEnt));
     L.elist = o;   o = align256(o + cap * eb);
     L.req = o;     o = align256(o + (prune ? cap * 16 : 0));
+    L.reqt = o;    o = align256(o + (prune ? cap * 4 : 0));    // trace index of each spill request
     L.trace = o;   o = align256(o + (prune ? cap * 2 * 8 : 0));   // Alg. 5's T: (v, t) pairs
     L.total = o;
     return L;

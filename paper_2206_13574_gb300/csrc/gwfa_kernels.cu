@@ -67,6 +67,7 @@ template <bool P> struct Slab {
     LEnt *qlist, *slist[2];
     EEntT<T> *elist;
     int4 *req;
+    uint32_t *reqt;
     uint2 *trace;
     uint32_t cap, mask;
 };
@@ -82,6 +83,7 @@ __device__ __forceinline__ Slab<P> carve(uint8_t *base, uint32_t log2cap) {
     s.slist[1] = (LEnt *)(base + L.slist1);
     s.elist = (EEntT<typename VT<P>::T> *)(base + L.elist);
     s.req = (int4 *)(base + L.req);
+    s.reqt = (uint32_t *)(base + L.reqt);
     s.trace = (uint2 *)(base + L.trace);
     s.cap = 1u << log2cap;
     s.mask = s.cap - 1;
@@ -418,6 +420,7 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
         if (ln == 0) m = atomicExch(&s.slots[ent.slot].reg[par], 0u);
         long long val = __ldcg(&s.slots[ent.slot].vals[ln]);
         const uint4 vi = __ldg(&g.vinfo[ent.v]);
+        const uint32_t tr = traceback ? __ldcg(&s.slots[ent.slot].trace[ln]) : 0u;
         m = __shfl_sync(gmask, m, 0, 8);
         if (ln == 0) {
             eidx = atomicAdd(&sh.ne, 1u);
@@ -437,17 +440,22 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
                 sh.found = 1;
                 // one 64-bit store, so that the vertex and its trace stay a pair when
                 // several diagonals reach a free end in the same score
-                sh.end_vp = ((unsigned long long)ent.v << 32) | pbase(val);
+                sh.end_vp = ((unsigned long long)ent.v << 32) | tr;
             }
             a = (unsigned long long)(k + j2) + pbase(val) + (unsigned)j2;   // a = i + W~ (Alg. 4)
             if ((uint32_t)j2 == vi.y) {
-                // payload of the spilled diagonals: the walk base (pruning) or the
-                // index of the T entry "left v with this trace" (traceback)
-                const uint32_t nb = traceback ? push_trace(s, sh, ent.v, pbase(val)) : pbase(val) + vi.y;
-                if (!traceback && nb > kBaseMask) set_err(sh, GWFA_ERR_CAPACITY);
+                // the spilled diagonals get the walk base past v and, with traceback,
+                // the index of the T entry "left v with this trace" (Alg. 5)
+                const uint32_t nb = pbase(val) + vi.y;
+                if (nb > kBaseMask) set_err(sh, GWFA_ERR_CAPACITY);
+                const uint32_t t = traceback ? push_trace(s, sh, ent.v, tr) : 0u;
                 const uint32_t r = atomicAdd(req_count, 1u);
-                if (r < s.cap) __stcg(&s.req[r], make_int4(k + (int)vi.y, (int)nb, (int)vi.z, (int)vi.w));
-                else set_err(sh, GWFA_ERR_CAPACITY);
+                if (r < s.cap) {
+                    __stcg(&s.req[r], make_int4(k + (int)vi.y, (int)nb, (int)vi.z, (int)vi.w));
+                    if (traceback) __stcg(&s.reqt[r], t);
+                } else {
+                    set_err(sh, GWFA_ERR_CAPACITY);
+                }
             }
         }
         for (int o = 4; o >= 1; o >>= 1) {
@@ -458,6 +466,7 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
         if (eidx < s.cap) {
             if (ln == 0) st_ehdr(&s.elist[eidx].hdr, ent.slot | (m << 24), ent.v, ent.kb, vi.y);
             __stcg(&s.elist[eidx].vals[ln], live ? val : -1ll);
+            if (traceback) __stcg(&s.elist[eidx].trace[ln], tr);
         } else if (ln == 0) {
             set_err(sh, GWFA_ERR_CAPACITY);
         }
@@ -481,6 +490,7 @@ __device__ void apply_spill_requests(const DevGraph &g, const Slab<true> &s, Sh 
             if (prev < 0) {
                 atomicAdd(&sh.visited, 1ull);
                 atomicAdd(&sh.spills, 1ull);
+                __stcg(&s.slots[su].trace[ku & 7], 0u);   // set by resolve_spill_traces
                 reg_append(&s.slots[su].reg[next_par], next_list, next_count, s.cap, (uint32_t)su, u, ku >> 3,
                            1u << (ku & 7), sh);
             }
@@ -488,13 +498,44 @@ __device__ void apply_spill_requests(const DevGraph &g, const Slab<true> &s, Sh 
     }
 }
 
+// Traceback with pruning: after apply_spill_requests (and a barrier) every diagonal
+// a spill inserted in this round holds the largest base among its spills, still
+// tagged pending; each request whose base is that one offers its T index and the
+// largest index wins (any of them is a walk of that base, so the choice only has to
+// be deterministic).
+__device__ void resolve_spill_traces(const DevGraph &g, const Slab<true> &s, Sh &sh, uint32_t n_req) {
+    const uint32_t nr = min(n_req, s.cap);
+    for (uint32_t r = threadIdx.x; r < nr; r += blockDim.x) {
+        const int4 rq = __ldcg(&s.req[r]);
+        const int ku = rq.x;
+        const long long cand = pk(0, kTagPend, (uint32_t)rq.y);
+        const uint32_t t = __ldcg(&s.reqt[r]);
+        for (uint32_t a = (uint32_t)rq.z; a < (uint32_t)rq.w; ++a) {
+            const int su = find_or_insert(s, sh, tile_key(__ldg(&g.arc_dst[a]), ku >> 3));
+            if (su < 0) return;
+            if (__ldcg(&s.slots[su].vals[ku & 7]) == cand) atomicMax(&s.slots[su].trace[ku & 7], t);
+        }
+    }
+}
+
+// Pruning mode: the merge of `cand` replaced `prev` and was the first of this
+// GwfExpand to do so (every offset is settled when GwfExpand starts, so the first
+// fresh value is the first change).
+__device__ __forceinline__ bool first_fresh(long long prev, long long cand) {
+    return cand > prev && ((prev >> 30) & 3) != kTagFresh;
+}
+__device__ __forceinline__ bool first_fresh(int, int) { return false; }
+
 // Offer value `cand` to lane `ln` of tile (slot, v, kb): GwfExpand's max-merge
 // into H~; the lane joins the next Q if its offset strictly improved.
 template <bool P>
 __device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, uint32_t v, int kb,
-                                      int ln, typename VT<P>::T cand, int par, uint32_t *qcount) {
+                                      int ln, typename VT<P>::T cand, int par, uint32_t *qcount, bool traceback) {
     const typename VT<P>::T prev = atomicMax(&s.slots[slot].vals[ln], cand);
     if (prev < 0) atomicAdd(&sh.visited, 1ull);
+    if constexpr (P) {
+        if (traceback && first_fresh(prev, cand)) __stcg(&s.slots[slot].trace[ln], 0u);
+    }
     if (pj(prev) < pj(cand)) reg_append(&s.slots[slot].reg[par], s.qlist, qcount, s.cap, slot, v, kb, 1u << ln, sh);
 }
 
@@ -503,7 +544,8 @@ __device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, u
 // their candidate max-merges are issued together before either registration.
 template <bool P>
 __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e, bool prune_on,
-                           long long amax, int max_lag, int par, uint32_t *qcount, uint32_t *claim) {
+                           long long amax, int max_lag, int par, uint32_t *qcount, uint32_t *claim,
+                           bool traceback) {
     using T = typename VT<P>::T;
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
@@ -568,6 +610,10 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
         for (int u = 0; u < 2; ++u) {
             if (!(valid[u] && cand[u] >= 0)) continue;
             if (prev[u] < 0) atomicAdd(&sh.visited, 1ull);
+            if constexpr (P) {
+                if (traceback && first_fresh(prev[u], cand[u]))
+                    __stcg(&s.slots[h[u].slot_mask & 0xFFFFFFu].trace[ln], 0u);
+            }
             if (pj(prev[u]) < pj(cand[u]))
                 reg_append(&s.slots[h[u].slot_mask & 0xFFFFFFu].reg[par], s.qlist, qcount, s.cap,
                            h[u].slot_mask & 0xFFFFFFu, h[u].v,
@@ -577,12 +623,63 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
         for (int u = 0; u < 2; ++u) {
             if (valid[u] && ln == 7 && ins[u]) {   // insertion leaves the tile: (v, 8(kb+1))
                 const int t = find_or_insert(s, sh, tile_key(h[u].v, h[u].kb + 1));
-                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb + 1, 0, c_ins[u], par, qcount);
+                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb + 1, 0, c_ins[u], par, qcount, traceback);
             }
             if (valid[u] && ln == 0 && del[u]) {   // deletion leaves the tile: (v, 8 kb - 1)
                 const int t = find_or_insert(s, sh, tile_key(h[u].v, h[u].kb - 1));
-                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb - 1, 7, c_del[u], par, qcount);
+                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb - 1, 7, c_del[u], par, qcount, traceback);
             }
+        }
+    }
+}
+
+// Traceback with pruning, after GwfExpand's merge (and a barrier): every diagonal
+// the merge raised holds the largest candidate (offset, base), tagged fresh; each
+// candidate equal to it offers the trace index of its source, and the largest
+// index wins (sources of equal offset and base are equally good predecessors).
+// The candidates and the pruning of their sources are recomputed as in expand_all.
+__device__ void resolve_expand_traces(const Slab<true> &s, Sh &sh, const QCtx &q, uint32_t n_e, bool prune_on,
+                                      long long amax, int max_lag, uint32_t *claim) {
+    const int ln = threadIdx.x & 7;
+    const unsigned gmask = 0xFFu << (threadIdx.x & 24);
+    const uint32_t ne = min(n_e, s.cap);
+    for (;;) {
+        const uint32_t e = group_claim(claim, 1u, gmask, ln);
+        if (e >= ne) break;
+        const EHdr h = ld_ehdr(&s.elist[e].hdr);
+        const long long val = __ldcg(&s.elist[e].vals[ln]);
+        const uint32_t tr = __ldcg(&s.elist[e].trace[ln]);
+        const uint32_t slot = h.slot_mask & 0xFFFFFFu;
+        bool act = (h.slot_mask >> (24 + ln)) & 1u;
+        const int k = h.kb * kTile + ln;
+        const int j = act ? pj(val) : 0;
+        const int i = k + j;
+        const uint32_t b = pbase(val);
+        if (act && prune_on && amax - ((long long)i + (long long)b + j) >= (long long)max_lag) act = false;
+        const bool ins = act && i < q.n;
+        const bool del = act && j < (int)h.lv;
+        const bool mis = ins && j < (int)h.lv;
+        const long long c_ins = ins ? pk(j, kTagFresh, b) : -1ll;
+        const long long c_del = del ? pk(j + 1, kTagFresh, b) : -1ll;
+        long long from_left = __shfl_up_sync(gmask, c_ins, 1, 8);
+        long long from_right = __shfl_down_sync(gmask, c_del, 1, 8);
+        const uint32_t t_left = __shfl_up_sync(gmask, tr, 1, 8);
+        const uint32_t t_right = __shfl_down_sync(gmask, tr, 1, 8);
+        if (ln == 0) from_left = -1;
+        if (ln == 7) from_right = -1;
+        if (mis || from_left >= 0 || from_right >= 0) {
+            const long long cur = __ldcg(&s.slots[slot].vals[ln]);
+            if (mis && cur == pk(j + 1, kTagFresh, b)) atomicMax(&s.slots[slot].trace[ln], tr);
+            if (from_left >= 0 && cur == from_left) atomicMax(&s.slots[slot].trace[ln], t_left);
+            if (from_right >= 0 && cur == from_right) atomicMax(&s.slots[slot].trace[ln], t_right);
+        }
+        if (ln == 7 && ins) {   // insertion left the tile: (v, 8(kb+1)), lane 0
+            const int t = find_or_insert(s, sh, tile_key(h.v, h.kb + 1));
+            if (t >= 0 && __ldcg(&s.slots[t].vals[0]) == c_ins) atomicMax(&s.slots[t].trace[0], tr);
+        }
+        if (ln == 0 && del) {   // deletion left the tile: (v, 8 kb - 1), lane 7
+            const int t = find_or_insert(s, sh, tile_key(h.v, h.kb - 1));
+            if (t >= 0 && __ldcg(&s.slots[t].vals[7]) == c_del) atomicMax(&s.slots[t].trace[7], tr);
         }
     }
 }
@@ -705,8 +802,12 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         const int slot = find_or_insert(s, sh, tile_key(vs, 0));
         if (slot >= 0) {
             typename VT<P>::T v0;
-            if constexpr (P) v0 = pk(0, kTagFresh, A.traceback ? kNoTrace : 0u);
-            else v0 = 0;
+            if constexpr (P) {
+                v0 = pk(0, kTagFresh, 0u);
+                s.slots[slot].trace[0] = kNoTrace;
+            } else {
+                v0 = 0;
+            }
             s.slots[slot].vals[0] = v0;
             sh.visited = 1;
             reg_append(&s.slots[slot].reg[1], s.qlist, &sh.nq[0], s.cap, (uint32_t)slot, vs, 0, 1u, sh);
@@ -728,8 +829,12 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             for (int ln = 0; ln < kTile; ++ln) {
                 if (!((bits >> ln) & 1u)) continue;
                 const int j = -(kb * kTile + ln);
-                if constexpr (P) s.slots[slot].vals[ln] = pk(j, kTagFresh, A.traceback ? kNoTrace : 0u);
-                else s.slots[slot].vals[ln] = j;
+                if constexpr (P) {
+                    s.slots[slot].vals[ln] = pk(j, kTagFresh, 0u);
+                    s.slots[slot].trace[ln] = kNoTrace;
+                } else {
+                    s.slots[slot].vals[ln] = j;
+                }
             }
             atomicAdd(&sh.visited, (unsigned long long)__popc(bits));
             reg_append(&s.slots[slot].reg[1], s.qlist, &sh.nq[0], s.cap, (uint32_t)slot, vs, kb, bits, sh);
@@ -786,6 +891,10 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                 if (threadIdx.x == 0) sh.nreq[(round + 1) & 1] = 0;
                 apply_spill_requests(g, s, sh, sh.nreq[round & 1], next_phase & 1, next_list,
                                      next_count);
+                if (A.traceback) {
+                    __syncthreads();
+                    resolve_spill_traces(g, s, sh, sh.nreq[round & 1]);
+                }
             } else {
                 extend_round_exact(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
                                    next_count, claim);
@@ -825,8 +934,21 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         }
         uint32_t *claim = &sh.claim[cstep % 3];
         ++cstep;
-        expand_all<P>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim);
+        expand_all<P>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
+                      A.traceback != 0);
         failed = __syncthreads_or(sh.err != 0);
+        if constexpr (P) {
+            if (A.traceback && !failed) {
+                if (threadIdx.x == 0) {
+                    sh.claim[(cstep + 1) % 3] = 0;
+                    sh.claim[(cstep + 2) % 3] = 0;
+                }
+                uint32_t *rclaim = &sh.claim[cstep % 3];
+                ++cstep;
+                resolve_expand_traces(s, sh, q, sh.ne, prune_on, amax, A.max_lag, rclaim);
+                failed = __syncthreads_or(sh.err != 0);
+            }
+        }
         if (A.stats) st_exp += globaltimer_ns() - t_exp;
         if (failed) break;
         if (sh.nq[d & 1] == 0) {
