@@ -272,7 +272,7 @@ int gwfa_align_batch_device(gwfa_engine *e, uint32_t n_queries, const uint32_t *
  * but its scratch is one fixed 32 MiB device array inside the library (present
  * on every GPU that loads it, until the process exits), carved into
  * floor((32 MiB - 256 B) / slab) CTA slabs of 2^log2_tiles hash tiles each
- * (log2_tiles 0 = 15: five CTAs in exact mode, three with pruning).  There is
+ * (log2_tiles 0 = 15: five CTAs in exact mode, two with pruning).  There is
  * no overflow tier: a query needing more than 3/4 of its slab gets status
  * GWFA_ERR_CAPACITY.  log2_tiles outside [8, 24] (other than 0) is
  * GWFA_ERR_INVALID; a valid log2_tiles whose slab does not fit the array is
@@ -357,10 +357,12 @@ typedef struct {
 
 /*
  * ctas: persistent CTAs (0 = 2 per SM); workspace_bytes: device scratch per CTA
- * (0 = 8 MiB).  A query needs 4 * (|sigma(w)| / 16 + 2) + 4 * (d + 1) * (d + 1 + L)
+ * (0 = 32 MiB).  Only every c-th pairwise wavefront is kept, c = ceil(sqrt(d + 1)),
+ * and the others are recomputed segment by segment during the backtrace, so a
+ * query needs 4 * (|sigma(w)| / 16 + 2) + 4 * (d / c + c + 2) * (2 d + L + 1)
  * bytes (the first term rounded up to 16; L = |first vertex| under GWFA_FREE_START,
- * else 0) of it: the default holds distances up to ~1400 for walks of tens of kb.  The workspace is allocated here; gwfa_cigar_device allocates
- * nothing.
+ * else 0): the default holds distances up to ~1.7 x 10^4 on walks of 100 kb.  The
+ * workspace is allocated here; gwfa_cigar_device allocates nothing.
  */
 int gwfa_cigar_create(const gwfa_graph *g, uint32_t ctas, uint64_t workspace_bytes, gwfa_cigar **out);
 int gwfa_cigar_destroy(gwfa_cigar *c);
@@ -461,7 +463,11 @@ int gwfa_plan_schedule(uint32_t n, const float *h_pred, uint64_t tier0_tiles, ui
  * (ctas_small, 2^log2_small tiles) and CTAs with large ones (ctas_big,
  * 2^log2_big); a request enters the class its predicted hash memory fits (the
  * attached cost model, else length > big_length), and a request that overflows
- * a small slab is re-queued into the large class automatically.  The kernel's
+ * a small slab is re-queued into the large class automatically.  Large-slab CTAs
+ * also take small requests whenever no large one waits.  The default configuration
+ * (gwfa_server_default_config) puts 2^17-tile slabs on 4 x SMs - SMs / 2 CTAs and
+ * 2^21-tile slabs on SMs / 2 CTAs of 512 threads (about 41 GB of device memory in
+ * exact mode, 2.3 times that with pruning).  The kernel's
  * CTAs leave together once all of them have been idle for idle_us (and in any
  * case after 16 x idle_us idle; every device wait is bounded), and the next
  * submit or poll starts it again.  Results are identical to gwfa_align.

@@ -168,6 +168,7 @@ int gwfa_graph_create(uint32_t nv, const char *h_seq, const uint64_t *h_seq_off,
         g->h_arc_off[v + 1] += g->h_arc_off[v];
     }
     for (size_t a = 0; a < arcs.size(); ++a) g->h_arc_dst[a] = arcs[a].second;
+    g->h_vlen = vlen;
 
     int st = cuda_status(cudaSetDevice(device));
     if (st) { delete g; return st; }

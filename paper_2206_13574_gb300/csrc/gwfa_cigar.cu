@@ -9,20 +9,27 @@
 //      (a block-wide prefix sum of the label lengths gives each vertex's position);
 //   2. for s = 0, 1, ... compute the furthest point of every diagonal k = j - i
 //      (i in the query, j in the walk) at score s from score s - 1 (substitution
-//      i+1, j+1; query base skipped i+1; walk base skipped j+1), extend it along
-//      equal bases 16 at a time (XOR of packed windows, first set bit), and keep
-//      every wavefront.  Score 0 starts at (0, 0), or at every (0, j) of the first
-//      vertex when the walk may start inside it (L = its length, else L = 0), so
-//      score s spans diagonals -s .. L + s and starts at offset s (L + s);
+//      i+1, j+1; query base skipped i+1; walk base skipped j+1) and extend it along
+//      equal bases 16 at a time (XOR of packed windows, first set bit).  Score 0
+//      starts at (0, 0), or at every (0, j) of the first vertex when the walk may
+//      start inside it (L = its length, else L = 0), so score s spans diagonals
+//      -s .. L + s.  Only every c-th wavefront is kept (a checkpoint), with
+//      c = ceil(sqrt(d + 1));
 //   3. once an end point is on a wavefront -- (n, m), or (n, j) for any j in the
-//      last vertex when the walk may end inside it -- one thread walks the stored
-//      wavefronts back: each step re-derives which predecessor gave the point's
-//      starting offset, emitting the run of equal bases and one edit.
+//      last vertex when the walk may end inside it -- the wavefronts are walked
+//      back one segment of c scores at a time, last segment first: the CTA
+//      recomputes the segment's wavefronts from its checkpoint (each is a
+//      deterministic function of the one before, so they are the forward pass's),
+//      then one thread steps back through them, each step re-deriving which
+//      predecessor gave the point's starting offset and emitting the run of equal
+//      bases and one edit.
 //
 // The score loop is bounded by the query's Gwfa distance d: when w is optimal,
 // the pairwise distance of q and sigma(w) (with the same free ends) is d (an
-// alignment of q to a walk is an alignment to its spelled sequence and back), so
-// (d + 1) (d + 1 + L) offsets suffice.
+// alignment of q to a walk is an alignment to its spelled sequence and back).
+// Rows are 2d + L + 1 offsets wide; ceil(d / c) + 1 checkpoints plus c segment
+// rows -- about 2 sqrt(d) rows instead of the d + 1 of keeping every wavefront --
+// so distances of 10^4 on 100 kb walks take ~16 MB, for twice the forward work.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -110,10 +117,44 @@ __device__ __forceinline__ Pred predecessors(const int *prev, int lo, int hi, in
     return p;
 }
 
-// wavefront s of a run whose score 0 spans diagonals 0 .. L: diagonals -s .. L + s,
-// stored from offset s (L + s), indexed by diagonal
-__device__ __forceinline__ int *wavefront(int *wf, int s, int L) {
-    return wf + (int64_t)s * (L + s) + s;
+// Stored wavefronts: fixed-width rows of W = 2d + L + 1 offsets, diagonal k of a
+// row at index k + d (score s only fills -s .. L + s).  Rows [0, n_ck) are the
+// checkpoints (score r * c in row r), rows n_ck .. n_ck + c - 1 the segment being
+// recomputed (score b + t in row n_ck + t; the forward pass uses two of them in
+// turn).
+struct Rows {
+    int *base;
+    int64_t width;
+    int d, c, n_ck;
+    __device__ int *row(int r) const { return base + (int64_t)r * width + d; }
+    __device__ int *checkpoint(int s) const { return row(s / c); }
+    __device__ int *segment(int t) const { return row(n_ck + t); }
+};
+
+// Wavefront s (diagonals -s .. L + s) from wavefront s - 1 (NULL for s = 0); true if
+// it reaches an end point, whose smallest diagonal goes to *s_hitk (shared memory;
+// NULL when recomputing a wavefront already known to reach none).
+__device__ bool wavefront_step(int s, const int *prev, int *cur, int L, int n, int m, const uint32_t *qw,
+                               const uint32_t *tw, bool free_end, int l_last, int k_end, int *s_hitk) {
+    bool hit = false;
+    for (int k = -s + (int)threadIdx.x; k <= L + s; k += blockDim.x) {
+        int c = -1;
+        if (s == 0) {
+            c = k >= 0 ? 0 : -1;   // (0, k): the walk entered k bases into its first vertex
+        } else {
+            const Pred p = predecessors(prev, -(s - 1), L + s - 1, k, n, m);
+            c = max(p.sub, max(p.ins, p.del));
+        }
+        int i = -1;
+        if (c >= 0 && c <= n && c + k >= 0 && c + k <= m)
+            i = c + run_length(qw, c, tw, c + k, min(n - c, m - c - k));
+        __stcg(cur + k, i);
+        if (s_hitk && i == n && (free_end ? n + k >= m - l_last && n + k <= m : k == k_end)) {
+            hit = true;
+            atomicMin(s_hitk, k);   // several end points: keep the smallest diagonal
+        }
+    }
+    return hit;
 }
 
 struct Runs {
@@ -172,7 +213,11 @@ __device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsig
     const int l_last = free_end && v_last < A.g.nv ? (int)__ldg(&A.g.vinfo[v_last]).y : 0;
     const uint64_t t_words = (m64 >> 4) + 2;
     const uint64_t wf_off = (t_words * 4 + 15) & ~15ull;
-    const uint64_t need = wf_off + (uint64_t)(d + 1) * (uint64_t)(d + 1 + L) * 4;
+    int seg = 1;   // c = ceil(sqrt(d + 1))
+    while ((int64_t)seg * seg < (int64_t)d + 1) ++seg;
+    const int n_ck = d / seg + 1;
+    const int64_t width = 2 * (int64_t)d + L + 1;
+    const uint64_t need = wf_off + (uint64_t)(n_ck + seg + 1) * (uint64_t)width * 4;
     o.walk_len = (uint32_t)min(m64, 0xFFFFFFFFull);
     if (m64 > 0x3FFFFFFFull || d < 0 || need > A.ws_bytes) {
         if (tid == 0) {
@@ -216,81 +261,93 @@ __device__ void align_walk(const CigarArgs &A, uint32_t qid, uint32_t *tw, unsig
         __syncthreads();
     }
 
-    // 2. wavefronts, score by score, until an end point is reached
-    int *wf = (int *)((uint8_t *)tw + wf_off);
+    // 2. wavefronts, score by score, until an end point is reached; checkpoints only
+    const Rows R{(int *)((uint8_t *)tw + wf_off), width, d, seg, n_ck};
     const uint32_t *qw = A.qwords + (A.q_off[qid] >> 4) + qid;
     const int k_end = m - n;
     if (tid == 0) s_hitk = 0x7FFFFFFF;
     __syncthreads();
     int found = -1;
+    const int *prev = nullptr;
     for (int s = 0; s <= d; ++s) {
-        int *cur = wavefront(wf, s, L);
-        const int *prev = s ? wavefront(wf, s - 1, L) : nullptr;
-        bool hit = false;
-        for (int k = -s + tid; k <= L + s; k += blockDim.x) {
-            int c = -1;
-            if (s == 0) {
-                c = k >= 0 ? 0 : -1;   // (0, k): the walk entered k bases into its first vertex
-            } else {
-                const Pred p = predecessors(prev, -(s - 1), L + s - 1, k, n, m);
-                c = max(p.sub, max(p.ins, p.del));
-            }
-            int i = -1;
-            if (c >= 0 && c <= n && c + k >= 0 && c + k <= m)
-                i = c + run_length(qw, c, tw, c + k, min(n - c, m - c - k));
-            __stcg(cur + k, i);
-            if (i == n && (free_end ? n + k >= m - l_last && n + k <= m : k == k_end)) {
-                hit = true;
-                atomicMin(&s_hitk, k);   // several end points: keep the smallest diagonal
-            }
-        }
+        int *cur = s % seg == 0 ? R.checkpoint(s) : R.segment(s & 1);
+        const bool hit = wavefront_step(s, prev, cur, L, n, m, qw, tw, free_end, l_last, k_end, &s_hitk);
         if (__syncthreads_or(hit)) {
             found = s;
             break;
         }
+        prev = cur;
     }
-
-    // 3. walk back from (n, m) to (0, 0)
-    if (tid == 0) {
-        if (found < 0) {
+    if (found < 0) {
+        if (tid == 0) {
             o.status = GWFA_ERR_SCORE_LIMIT;
             A.out[qid] = o;
-            return;
         }
-        Runs R{A.cigar + (uint64_t)qid * A.cigar_cap, A.cigar_cap, 0u, 0u, 0u};
-        int s = found, k = s_hitk, i = n;
-        o.walk_end = (uint32_t)(n + k);
-        while (s > 0) {
-            const int *prev = wavefront(wf, s - 1, L);
-            const Pred p = predecessors(prev, -(s - 1), L + s - 1, k, n, m);
-            const int c = max(p.sub, max(p.ins, p.del));
-            R.emit(GWFA_CIGAR_EQ, (uint32_t)(i - c));
-            if (p.sub == c) {
-                R.emit(GWFA_CIGAR_DIFF, 1u);
-                i = c - 1;
-            } else if (p.ins == c) {
-                R.emit(GWFA_CIGAR_INS, 1u);
-                i = c - 1;
-                k = k + 1;
-            } else {
-                R.emit(GWFA_CIGAR_DEL, 1u);
-                i = c;
-                k = k - 1;
+        return;
+    }
+
+    // 3. walk back from the end point to score 0, one segment of c scores at a
+    // time, last first: wavefronts b + 1 .. b + c - 1 are recomputed from the
+    // checkpoint b, then the steps of scores b + c .. b + 1 read them
+    __shared__ int s_i, s_k;
+    __shared__ uint32_t s_nops, s_op, s_len;
+    if (tid == 0) {
+        s_i = n;
+        s_k = s_hitk;
+        s_nops = s_op = s_len = 0;
+        o.walk_end = (uint32_t)(n + s_hitk);
+    }
+    for (int b = ((found - 1) / seg) * seg; found > 0 && b >= 0; b -= seg) {
+        const int top = min(b + seg, found);   // steps s = top .. b + 1 read rows top - 1 .. b
+        for (int r = b + 1; r <= top - 1; ++r) {
+            const int *pr = r - 1 == b ? R.checkpoint(b) : R.segment(r - 1 - b);
+            wavefront_step(r, pr, R.segment(r - b), L, n, m, qw, tw, false, 0, 0, nullptr);
+            __syncthreads();
+        }
+        if (tid == 0) {
+            Runs Rn{A.cigar + (uint64_t)qid * A.cigar_cap, A.cigar_cap, s_nops, s_op, s_len};
+            int i = s_i, k = s_k;
+            for (int s = top; s > b; --s) {
+                const int *pv = s - 1 == b ? R.checkpoint(b) : R.segment(s - 1 - b);
+                const Pred p = predecessors(pv, -(s - 1), L + s - 1, k, n, m);
+                const int c = max(p.sub, max(p.ins, p.del));
+                Rn.emit(GWFA_CIGAR_EQ, (uint32_t)(i - c));
+                if (p.sub == c) {
+                    Rn.emit(GWFA_CIGAR_DIFF, 1u);
+                    i = c - 1;
+                } else if (p.ins == c) {
+                    Rn.emit(GWFA_CIGAR_INS, 1u);
+                    i = c - 1;
+                    k = k + 1;
+                } else {
+                    Rn.emit(GWFA_CIGAR_DEL, 1u);
+                    i = c;
+                    k = k - 1;
+                }
             }
-            --s;
+            s_i = i;
+            s_k = k;
+            s_nops = Rn.n;
+            s_op = Rn.op;
+            s_len = Rn.len;
         }
-        R.emit(GWFA_CIGAR_EQ, (uint32_t)i);   // score 0: equal bases from (0, k)
-        R.flush();
+        __syncthreads();
+    }
+    if (tid == 0) {
+        Runs Rn{A.cigar + (uint64_t)qid * A.cigar_cap, A.cigar_cap, s_nops, s_op, s_len};
+        const int i = s_i, k = s_k;
+        Rn.emit(GWFA_CIGAR_EQ, (uint32_t)i);   // score 0: equal bases from (0, k)
+        Rn.flush();
         o.walk_begin = (uint32_t)k;
-        if (R.n <= R.cap)   // emitted end to start: reverse in place
-            for (uint32_t a = 0, b = R.n; a + 1 < b; ++a, --b) {
-                const uint32_t t = R.ops[a];
-                R.ops[a] = R.ops[b - 1];
-                R.ops[b - 1] = t;
+        if (Rn.n <= Rn.cap)   // emitted end to start: reverse in place
+            for (uint32_t a = 0, e = Rn.n; a + 1 < e; ++a, --e) {
+                const uint32_t t = Rn.ops[a];
+                Rn.ops[a] = Rn.ops[e - 1];
+                Rn.ops[e - 1] = t;
             }
         o.cost = found;
-        o.n_ops = R.n;
-        o.status = R.n <= R.cap ? GWFA_OK : GWFA_ERR_CAPACITY;
+        o.n_ops = Rn.n;
+        o.status = Rn.n <= Rn.cap ? GWFA_OK : GWFA_ERR_CAPACITY;
         A.out[qid] = o;
     }
 }
@@ -325,7 +382,7 @@ extern "C" int gwfa_cigar_create(const gwfa_graph *g, uint32_t ctas, uint64_t wo
             return GWFA_ERR_CUDA;
         ctas = 2u * (uint32_t)sms;
     }
-    if (workspace_bytes == 0) workspace_bytes = 8ull << 20;
+    if (workspace_bytes == 0) workspace_bytes = 32ull << 20;
     workspace_bytes = (workspace_bytes + 255) & ~255ull;
     gwfa_cigar *c = new (std::nothrow) gwfa_cigar();
     if (!c) return GWFA_ERR_OOM;

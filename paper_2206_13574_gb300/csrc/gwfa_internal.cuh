@@ -185,7 +185,7 @@ struct gwfa_graph {
     uint64_t na = 0, total = 0, n_words = 0;
     uint32_t max_outdeg = 0;
     int has_cycles = 0;
-    std::vector<uint32_t> h_arc_off, h_arc_dst;
+    std::vector<uint32_t> h_arc_off, h_arc_dst, h_vlen;
     uint32_t *d_words = nullptr, *d_arc_dst = nullptr;
     uint4 *d_vinfo = nullptr;
     uint64_t device_bytes = 0;

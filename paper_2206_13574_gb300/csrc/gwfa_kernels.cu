@@ -1061,7 +1061,9 @@ __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned l
 
 // Serving: a persistent kernel whose CTAs take requests from host-published rings
 // (continuous batching: a CTA starts a new request as soon as it finishes one).
-// CTAs [0, n_small) serve class 0 (small hash slabs), the rest class 1.  Every
+// CTAs [0, n_small) serve class 0 (small hash slabs), the rest class 1 (large
+// slabs), which also take class-0 requests whenever no class-1 request waits, so
+// large slabs are never left idle while small requests queue.  Every
 // wait is bounded: a CTA idle for wait_limit polls votes idle (and withdraws the
 // vote if work comes); the CTAs leave together once every CTA has voted, or after
 // 16 x wait_limit polls in any case, and the host relaunches the kernel when work
@@ -1073,7 +1075,7 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
     __shared__ unsigned long long s_ticket;
     __shared__ uint64_t s_qoff[2];
     __shared__ uint32_t s_vs, s_ve;
-    __shared__ int s_go;
+    __shared__ int s_go, s_ring;
     const int cls = blockIdx.x < S.n_small ? 0 : 1;
     uint8_t *base = cls == 0 ? S.slabs + (uint64_t)blockIdx.x * S.slab_bytes[0]
                              : S.slabs + S.big_offset + (uint64_t)(blockIdx.x - S.n_small) * S.slab_bytes[1];
@@ -1085,16 +1087,26 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
             bool voted = false;
             for (;;) {
                 if (ld_acquire_sys(S.stop)) break;
-                const unsigned long long h = atomicAdd(S.head + cls, 0ull);
-                const unsigned long long t = ld_acquire_sys(S.tail[cls]);
-                if (h < t) {
+                // the CTA's own ring first; a large-slab CTA then looks at ring 0
+                int rc = -1;
+                unsigned long long h = 0;
+                for (int c = cls; c >= 0; --c) {
+                    const unsigned long long hc = atomicAdd(S.head + c, 0ull);
+                    if (hc < ld_acquire_sys(S.tail[c])) {
+                        rc = c;
+                        h = hc;
+                        break;
+                    }
+                }
+                if (rc >= 0) {
                     if (voted) {
                         atomicSub(S.idle_votes, 1u);
                         voted = false;
                     }
                     polls = 0;
-                    if (atomicCAS(S.head + cls, h, h + 1) == h) {
+                    if (atomicCAS(S.head + rc, h, h + 1) == h) {
                         s_ticket = h;
+                        s_ring = rc;
                         go = 1;
                         break;
                     }
@@ -1116,11 +1128,12 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
         __syncthreads();
         if (!s_go) break;
         const unsigned long long ticket = s_ticket;
+        const int rc = s_ring;   // the ring the request came from (its result goes back there)
         const uint32_t slot = (uint32_t)(ticket % S.ring);
-        const ReqDesc *d = S.desc[cls] + slot;
+        const ReqDesc *d = S.desc[rc] + slot;
         const uint32_t n = __ldcv(&d->n);
         const uint32_t nw = (n + 15) >> 4;
-        const uint32_t *src = S.arena[cls] + (uint64_t)slot * S.slot_words;
+        const uint32_t *src = S.arena[rc] + (uint64_t)slot * S.slot_words;
         for (uint32_t w = threadIdx.x; w < nw + 2; w += blockDim.x) qsm[w] = w < nw ? __ldcv(src + w) : 0u;
         if (threadIdx.x == 0) {
             s_qoff[0] = 0;
@@ -1136,13 +1149,13 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
         A.q_off = s_qoff;
         A.v_s = &s_vs;
         A.v_e = &s_ve;
-        A.out = S.results[cls] + slot;
+        A.out = S.results[rc] + slot;
         A.max_lag = S.max_lag;
         A.max_score = S.max_score;
         align_one<P>(A, s, sh, 0);
         if (threadIdx.x == 0) {
             __threadfence_system();
-            st_release_sys(S.done[cls] + slot, ticket + 1);
+            st_release_sys(S.done[rc] + slot, ticket + 1);
         }
         __syncthreads();
     }

@@ -21,6 +21,8 @@
 #include <cmath>
 #include <mutex>
 #include <new>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "gwfa_internal.cuh"
@@ -42,11 +44,126 @@ constexpr int SAMPLES = 64; // query k-mers sampled per query
 struct FeatGraph {
     const uint32_t *kmers;   // sorted distinct 16-mers inside vertex labels (2-bit packed)
     uint64_t n_kmers;
-    const uint32_t *bub;     // prefix count of vertices with out-degree > 1, nv + 1
-    const uint32_t *back;    // prefix count of arcs u -> v with v <= u, by source, nv + 1
     const uint4 *vinfo;      // {word, len, arc_begin, arc_end} as in the alignment kernels
+    const uint32_t *arc_dst; // out-arc targets (CSR of the graph)
+    const uint32_t *in_off;  // in-arcs: CSR by target, nv + 1
+    const uint32_t *in_src;
+    const uint8_t *arc_cyc;  // 1 for an out-arc inside a strongly connected component
     uint32_t nv;
 };
+
+// ---- the co-reachable subgraph of a query
+//
+// S = the vertices on some v_s -> v_e walk whose spelled length stays within the
+// budget B = ceil(1.25 |q|) + 64 (the query's own walk spells about |q| bases;
+// walks much longer than the query cannot be its alignment).  With f(v) = the
+// shortest spelled length from v_s up to (not including) v and b(v) = the same from
+// just after v to the end of v_e, v is in S iff f(v) + |v| + b(v) <= B.  Both are
+// found by bounded label-correcting searches (forward from v_s, backward from v_e
+// over in-arcs), whose result is the exact shortest lengths within the budget in
+// any processing order.  The counts: |S|; arcs with both ends in S; vertices of S
+// with two or more such arcs (bubble openings); such arcs inside a strongly
+// connected component (loops).  A search that outgrows its table stops inserting
+// and the counts cover what it reached.
+constexpr uint32_t kSetCap = 8192;          // table entries per search (power of two)
+constexpr uint32_t kSetLoad = kSetCap / 4 * 3;
+constexpr uint32_t kFeatWarps = 1216;       // warps of the features kernel (8 per SM on 152 SMs)
+constexpr uint32_t kEmptyV = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint64_t feature_budget(uint64_t n) { return (5 * n + 3) / 4 + 64; }
+
+// per-warp scratch: two tables (forward, backward) of (vertex, length) and two
+// frontiers, in global memory
+struct SetScratch {
+    uint32_t *key[2], *dist[2], *fr[2];
+};
+__device__ __forceinline__ SetScratch set_scratch(uint32_t *base, uint32_t warp) {
+    uint32_t *w = base + (uint64_t)warp * 6 * kSetCap;
+    return SetScratch{{w, w + kSetCap}, {w + 2 * kSetCap, w + 3 * kSetCap}, {w + 4 * kSetCap, w + 5 * kSetCap}};
+}
+
+__device__ __forceinline__ uint32_t vhash(uint32_t v) { return (v * 0x9E3779B1u) & (kSetCap - 1); }
+
+// slot of v in table t (inserted with length ~0 when absent), or -1 when full
+__device__ int set_insert(const SetScratch &S, int t, uint32_t v, uint32_t *fill) {
+    uint32_t h = vhash(v);
+    for (uint32_t p = 0; p < kSetCap; ++p) {
+        const uint32_t k = __ldcg(&S.key[t][h]);
+        if (k == v) return (int)h;
+        if (k == kEmptyV) {
+            if (atomicAdd(fill, 0u) >= kSetLoad) return -1;
+            const uint32_t prev = atomicCAS(&S.key[t][h], kEmptyV, v);
+            if (prev == kEmptyV) {
+                atomicAdd(fill, 1u);
+                return (int)h;
+            }
+            if (prev == v) return (int)h;
+        }
+        h = (h + 1) & (kSetCap - 1);
+    }
+    return -1;
+}
+__device__ uint32_t set_find(const SetScratch &S, int t, uint32_t v) {
+    uint32_t h = vhash(v);
+    for (uint32_t p = 0; p < kSetCap; ++p) {
+        const uint32_t k = __ldcg(&S.key[t][h]);
+        if (k == v) return __ldcg(&S.dist[t][h]);
+        if (k == kEmptyV) return kEmptyV;
+        h = (h + 1) & (kSetCap - 1);
+    }
+    return kEmptyV;
+}
+
+// Bounded search of one warp: t = 0 forward from `src` over out-arcs, t = 1
+// backward over in-arcs; lengths are spelled bases strictly before (forward) or
+// after (backward) a vertex.
+__device__ void bounded_search(const FeatGraph &fg, const SetScratch &S, int t, uint32_t src, uint64_t budget,
+                               uint32_t *cnt /* shared: fill, frontier sizes [2] */) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i = lane; i < kSetCap; i += 32) {
+        __stcg(&S.key[t][i], kEmptyV);
+        __stcg(&S.dist[t][i], kEmptyV);
+    }
+    if (lane == 0) {
+        cnt[0] = 0;
+        cnt[1] = 1;
+        cnt[2] = 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int h = set_insert(S, t, src, &cnt[0]);
+        if (h >= 0) __stcg(&S.dist[t][h], 0u);
+        __stcg(&S.fr[0][0], src);
+    }
+    __syncwarp();
+    for (int cur = 0;; cur ^= 1) {
+        const uint32_t nf = min(cnt[1 + cur], kSetCap);
+        if (nf == 0) break;
+        for (uint32_t i = lane; i < nf; i += 32) {
+            const uint32_t v = __ldcg(&S.fr[cur][i]);
+            const uint32_t dv = set_find(S, t, v);
+            const uint4 vi = __ldg(&fg.vinfo[v]);
+            // forward: a successor starts |v| bases later; backward: a predecessor u
+            // ends where v starts, so its length after it is b(v) + |v|
+            const uint64_t cand = (uint64_t)dv + vi.y;
+            if (cand > budget) continue;
+            const uint32_t a0 = t == 0 ? vi.z : __ldg(&fg.in_off[v]);
+            const uint32_t a1 = t == 0 ? vi.w : __ldg(&fg.in_off[v + 1]);
+            for (uint32_t a = a0; a < a1; ++a) {
+                const uint32_t u = t == 0 ? __ldg(&fg.arc_dst[a]) : __ldg(&fg.in_src[a]);
+                const int h = set_insert(S, t, u, &cnt[0]);
+                if (h < 0) continue;
+                if (atomicMin(&S.dist[t][h], (uint32_t)cand) > (uint32_t)cand) {
+                    const uint32_t k = atomicAdd(&cnt[2 - cur], 1u);
+                    if (k < kSetCap) __stcg(&S.fr[cur ^ 1][k], u);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) cnt[1 + cur] = 0;
+        __syncwarp();
+    }
+}
 
 __device__ __forceinline__ uint32_t qwindow16(const uint32_t *w, uint64_t p) {
     const uint64_t wi = p >> 4;
@@ -68,17 +185,20 @@ __device__ bool kmer_present(const uint32_t *a, uint64_t n, uint32_t key) {
 // Raw features of each query (one warp per query, two sampled k-mers per lane):
 //   0 log1p(|q|)
 //   1 fraction of 64 evenly spaced query 16-mers absent from the graph's labels
-//   2 log1p(vertices with id in [v_s, v_e])  -- the id interval, which is the
-//     s->e subgraph when ids follow the graph's topological order
-//   3 log1p(arcs leaving that interval's vertices)
-//   4 vertices with out-degree > 1 in the interval, per kb of query
-//   5 log1p(back arcs (to an equal or lower id) leaving the interval)
+//   2 log1p(|S|), S the co-reachable subgraph above
+//   3 log1p(arcs inside S)
+//   4 vertices of S with two or more arcs inside S, per kb of query
+//   5 log1p(arcs inside S that lie on a cycle)
 __global__ void features_kernel(FeatGraph fg, uint32_t nq, const uint32_t *__restrict__ words,
                                 const uint64_t *__restrict__ q_off, const uint32_t *__restrict__ vs,
-                                const uint32_t *__restrict__ ve, float *__restrict__ feat) {
+                                const uint32_t *__restrict__ ve, float *__restrict__ feat,
+                                uint32_t *__restrict__ scratch) {
+    __shared__ uint32_t s_cnt[8][3];
     const int lane = threadIdx.x & 31;
     const uint32_t wpb = blockDim.x >> 5;
-    for (uint32_t qi = blockIdx.x * wpb + (threadIdx.x >> 5); qi < nq; qi += gridDim.x * wpb) {
+    const uint32_t wib = threadIdx.x >> 5;
+    const SetScratch S = set_scratch(scratch, blockIdx.x * wpb + wib);
+    for (uint32_t qi = blockIdx.x * wpb + wib; qi < nq; qi += gridDim.x * wpb) {
         const uint64_t qo = q_off[qi];
         const uint64_t n = q_off[qi + 1] - qo;
         const uint32_t *qw = words + (qo >> 4) + qi;
@@ -90,23 +210,44 @@ __global__ void features_kernel(FeatGraph fg, uint32_t nq, const uint32_t *__res
             }
         }
         for (int o = 16; o >= 1; o >>= 1) miss += __shfl_xor_sync(0xFFFFFFFFu, miss, o);
+        // the co-reachable subgraph
+        const uint32_t a = min(vs[qi], fg.nv - 1), b = min(ve[qi], fg.nv - 1);
+        const uint64_t budget = feature_budget(n);
+        bounded_search(fg, S, 0, a, budget, s_cnt[wib]);
+        bounded_search(fg, S, 1, b, budget, s_cnt[wib]);
+        uint32_t nverts = 0, narcs = 0, nbub = 0, ncyc = 0;
+        for (uint32_t i = lane; i < kSetCap; i += 32) {
+            const uint32_t v = __ldcg(&S.key[0][i]);
+            if (v == kEmptyV) continue;
+            const uint32_t fv = __ldcg(&S.dist[0][i]), bv = set_find(S, 1, v);
+            const uint4 vi = __ldg(&fg.vinfo[v]);
+            if (bv == kEmptyV || (uint64_t)fv + vi.y + bv > budget) continue;
+            ++nverts;
+            uint32_t deg = 0;
+            for (uint32_t e = vi.z; e < vi.w; ++e) {
+                const uint32_t u = __ldg(&fg.arc_dst[e]);
+                const uint32_t fu = set_find(S, 0, u), bu = set_find(S, 1, u);
+                if (fu == kEmptyV || bu == kEmptyV || (uint64_t)fu + __ldg(&fg.vinfo[u]).y + bu > budget) continue;
+                ++deg;
+                ncyc += __ldg(&fg.arc_cyc[e]);
+            }
+            narcs += deg;
+            nbub += deg > 1 ? 1u : 0u;
+        }
+        nverts = __reduce_add_sync(0xFFFFFFFFu, nverts);
+        narcs = __reduce_add_sync(0xFFFFFFFFu, narcs);
+        nbub = __reduce_add_sync(0xFFFFFFFFu, nbub);
+        ncyc = __reduce_add_sync(0xFFFFFFFFu, ncyc);
         if (lane == 0) {
-            uint32_t a = vs[qi], b = ve[qi];
-            if (a >= fg.nv) a = fg.nv - 1;
-            if (b >= fg.nv) b = fg.nv - 1;
-            const uint32_t lo = min(a, b), hi = max(a, b);
-            const float nverts = (float)(hi - lo + 1);
-            const float narcs = (float)(fg.vinfo[hi].w - fg.vinfo[lo].z);
-            const float nbub = (float)(fg.bub[hi + 1] - fg.bub[lo]);
-            const float nback = (float)(fg.back[hi + 1] - fg.back[lo]);
             float *f = feat + (uint64_t)qi * F;
             f[0] = log1pf((float)n);
             f[1] = n >= K ? (float)miss / SAMPLES : 0.f;
-            f[2] = log1pf(nverts);
-            f[3] = log1pf(narcs);
-            f[4] = nbub * 1000.f / (float)max(n, (uint64_t)1);
-            f[5] = log1pf(nback);
+            f[2] = log1pf((float)nverts);
+            f[3] = log1pf((float)narcs);
+            f[4] = (float)nbub * 1000.f / (float)max(n, (uint64_t)1);
+            f[5] = log1pf((float)ncyc);
         }
+        __syncwarp();
     }
 }
 
@@ -256,10 +397,12 @@ uint64_t splitmix(uint64_t &s) {
 struct gwfa_model {
     const gwfa_graph *g = nullptr;
     // host copies for predicting single requests on the host (serving admission)
-    std::vector<uint32_t> h_kmers, h_bub, h_back;
+    std::vector<uint32_t> h_kmers, h_in_off, h_in_src;
+    std::vector<uint8_t> h_arc_cyc;
     std::vector<float> h_w;
     FeatGraph fg{};
-    uint32_t *d_kmers = nullptr, *d_bub = nullptr, *d_back = nullptr;
+    uint32_t *d_kmers = nullptr, *d_in_off = nullptr, *d_in_src = nullptr, *d_scratch = nullptr;
+    uint8_t *d_arc_cyc = nullptr;
     float *d_w = nullptr, *d_m = nullptr, *d_v = nullptr, *d_g = nullptr, *d_loss = nullptr;
     __half *d_w16 = nullptr;
     uint32_t *d_idx = nullptr;
@@ -269,6 +412,107 @@ struct gwfa_model {
     cudaStream_t stream = nullptr;
     std::mutex mu;
 };
+
+// Strongly connected components (iterative Tarjan): component id per vertex.
+static std::vector<uint32_t> strong_components(uint32_t nv, const std::vector<uint32_t> &off,
+                                        const std::vector<uint32_t> &dst) {
+    const uint32_t none = 0xFFFFFFFFu;
+    std::vector<uint32_t> index(nv, none), low(nv, 0), comp(nv, none), stack;
+    std::vector<uint8_t> on(nv, 0);
+    std::vector<std::pair<uint32_t, uint32_t>> call;   // (vertex, next arc)
+    uint32_t next_index = 0, next_comp = 0;
+    for (uint32_t r = 0; r < nv; ++r) {
+        if (index[r] != none) continue;
+        call.push_back({r, off[r]});
+        index[r] = low[r] = next_index++;
+        stack.push_back(r);
+        on[r] = 1;
+        while (!call.empty()) {
+            const uint32_t v = call.back().first;
+            uint32_t &a = call.back().second;
+            if (a < off[v + 1]) {
+                const uint32_t w = dst[a++];
+                if (index[w] == none) {
+                    index[w] = low[w] = next_index++;
+                    stack.push_back(w);
+                    on[w] = 1;
+                    call.push_back({w, off[w]});
+                } else if (on[w]) {
+                    low[v] = std::min(low[v], index[w]);
+                }
+                continue;
+            }
+            call.pop_back();
+            if (!call.empty()) low[call.back().first] = std::min(low[call.back().first], low[v]);
+            if (low[v] == index[v]) {
+                uint32_t w;
+                do {
+                    w = stack.back();
+                    stack.pop_back();
+                    on[w] = 0;
+                    comp[w] = next_comp;
+                } while (w != v);
+                ++next_comp;
+            }
+        }
+    }
+    return comp;
+}
+
+// The co-reachable subgraph counts of the features kernel, on the host (serving
+// admission): |S|, arcs inside S, vertices with two or more of them, cycle arcs.
+static void coreachable_counts(const gwfa_model *m, uint32_t vs, uint32_t ve, uint64_t n, uint32_t out[4]) {
+    const gwfa_graph *g = m->g;
+    const uint64_t budget = (5 * n + 3) / 4 + 64;
+    auto len = [&](uint32_t v) { return (uint64_t)(g->h_vlen[v]); };
+    auto search = [&](uint32_t src, bool fwd) {
+        std::unordered_map<uint32_t, uint64_t> dist;
+        std::vector<uint32_t> cur{src}, nxt;
+        dist[src] = 0;
+        while (!cur.empty()) {
+            nxt.clear();
+            for (uint32_t v : cur) {
+                const uint64_t c = dist[v] + len(v);
+                if (c > budget) continue;
+                const uint32_t a0 = fwd ? g->h_arc_off[v] : m->h_in_off[v];
+                const uint32_t a1 = fwd ? g->h_arc_off[v + 1] : m->h_in_off[v + 1];
+                for (uint32_t a = a0; a < a1; ++a) {
+                    const uint32_t u = fwd ? g->h_arc_dst[a] : m->h_in_src[a];
+                    auto it = dist.find(u);
+                    if (it == dist.end() || c < it->second) {
+                        dist[u] = c;
+                        nxt.push_back(u);
+                    }
+                }
+            }
+            std::swap(cur, nxt);
+        }
+        return dist;
+    };
+    const auto f = search(vs, true), b = search(ve, false);
+    auto in_s = [&](uint32_t v) {
+        auto i = f.find(v), j = b.find(v);
+        return i != f.end() && j != b.end() && i->second + len(v) + j->second <= budget;
+    };
+    uint32_t nverts = 0, narcs = 0, nbub = 0, ncyc = 0;
+    for (const auto &kv : f) {
+        const uint32_t v = kv.first;
+        if (!in_s(v)) continue;
+        ++nverts;
+        uint32_t deg = 0;
+        for (uint32_t a = g->h_arc_off[v]; a < g->h_arc_off[v + 1]; ++a) {
+            if (!in_s(g->h_arc_dst[a])) continue;
+            ++deg;
+            ncyc += m->h_arc_cyc[a];
+        }
+        narcs += deg;
+        nbub += deg > 1 ? 1 : 0;
+    }
+    out[0] = nverts;
+    out[1] = narcs;
+    out[2] = nbub;
+    out[3] = ncyc;
+}
 
 extern "C" {
 
@@ -297,20 +541,29 @@ int gwfa_model_create(const gwfa_graph *g, uint64_t seed, gwfa_model **out) {
     }
     std::sort(kmers.begin(), kmers.end());
     kmers.erase(std::unique(kmers.begin(), kmers.end()), kmers.end());
-    std::vector<uint32_t> bub(g->nv + 1, 0), back(g->nv + 1, 0);
-    for (uint32_t v = 0; v < g->nv; ++v) {
-        const uint32_t deg = g->h_arc_off[v + 1] - g->h_arc_off[v];
-        uint32_t nb = 0;
-        for (uint32_t a = g->h_arc_off[v]; a < g->h_arc_off[v + 1]; ++a) nb += g->h_arc_dst[a] <= v;
-        bub[v + 1] = bub[v] + (deg > 1 ? 1 : 0);
-        back[v + 1] = back[v] + nb;
+    // in-arcs (CSR by target) for the backward search, and which arcs lie on a cycle
+    const uint64_t na = g->h_arc_dst.size();
+    std::vector<uint32_t> in_off(g->nv + 1, 0), in_src(na);
+    for (uint64_t a = 0; a < na; ++a) in_off[g->h_arc_dst[a] + 1]++;
+    for (uint32_t v = 0; v < g->nv; ++v) in_off[v + 1] += in_off[v];
+    {
+        std::vector<uint32_t> pos(in_off.begin(), in_off.end() - 1);
+        for (uint32_t v = 0; v < g->nv; ++v)
+            for (uint32_t a = g->h_arc_off[v]; a < g->h_arc_off[v + 1]; ++a) in_src[pos[g->h_arc_dst[a]]++] = v;
     }
+    const std::vector<uint32_t> comp = strong_components(g->nv, g->h_arc_off, g->h_arc_dst);
+    std::vector<uint8_t> arc_cyc(std::max<uint64_t>(na, 1), 0);
+    for (uint32_t v = 0; v < g->nv; ++v)
+        for (uint32_t a = g->h_arc_off[v]; a < g->h_arc_off[v + 1]; ++a)
+            arc_cyc[a] = comp[v] == comp[g->h_arc_dst[a]] ? 1 : 0;
     gwfa_model *m = new (std::nothrow) gwfa_model();
     if (!m) return GWFA_ERR_OOM;
     m->g = g;
     st = cstat(cudaMalloc(&m->d_kmers, std::max<uint64_t>(kmers.size(), 1) * 4));
-    if (!st) st = cstat(cudaMalloc(&m->d_bub, (uint64_t)(g->nv + 1) * 4));
-    if (!st) st = cstat(cudaMalloc(&m->d_back, (uint64_t)(g->nv + 1) * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_in_off, (uint64_t)(g->nv + 1) * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_in_src, std::max<uint64_t>(na, 1) * 4));
+    if (!st) st = cstat(cudaMalloc(&m->d_arc_cyc, arc_cyc.size()));
+    if (!st) st = cstat(cudaMalloc(&m->d_scratch, (uint64_t)kFeatWarps * 6 * kSetCap * 4));
     if (!st) st = cstat(cudaMalloc(&m->d_w, NPARAM * 4));
     if (!st) st = cstat(cudaMalloc(&m->d_m, NPARAM * 4));
     if (!st) st = cstat(cudaMalloc(&m->d_v, NPARAM * 4));
@@ -320,13 +573,16 @@ int gwfa_model_create(const gwfa_graph *g, uint64_t seed, gwfa_model **out) {
     if (!st) st = cstat(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
     if (!st && !kmers.empty())
         st = cstat(cudaMemcpy(m->d_kmers, kmers.data(), kmers.size() * 4, cudaMemcpyHostToDevice));
-    if (!st) st = cstat(cudaMemcpy(m->d_bub, bub.data(), bub.size() * 4, cudaMemcpyHostToDevice));
-    if (!st) st = cstat(cudaMemcpy(m->d_back, back.data(), back.size() * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cstat(cudaMemcpy(m->d_in_off, in_off.data(), in_off.size() * 4, cudaMemcpyHostToDevice));
+    if (!st && na) st = cstat(cudaMemcpy(m->d_in_src, in_src.data(), na * 4, cudaMemcpyHostToDevice));
+    if (!st) st = cstat(cudaMemcpy(m->d_arc_cyc, arc_cyc.data(), arc_cyc.size(), cudaMemcpyHostToDevice));
     if (st) { gwfa_model_destroy(m); return st; }
-    m->fg = FeatGraph{m->d_kmers, kmers.size(), m->d_bub, m->d_back, g->d_vinfo, g->nv};
+    m->fg = FeatGraph{m->d_kmers, kmers.size(), g->d_vinfo, g->d_arc_dst, m->d_in_off, m->d_in_src,
+                      m->d_arc_cyc, g->nv};
     m->h_kmers = std::move(kmers);
-    m->h_bub = std::move(bub);
-    m->h_back = std::move(back);
+    m->h_in_off = std::move(in_off);
+    m->h_in_src = std::move(in_src);
+    m->h_arc_cyc = std::move(arc_cyc);
     // He-style initialisation from a seeded SplitMix64 stream
     std::vector<float> w(NPARAM, 0.f);
     uint64_t s = seed;
@@ -346,8 +602,10 @@ int gwfa_model_destroy(gwfa_model *m) {
     if (!m) return GWFA_ERR_INVALID;
     cudaSetDevice(m->g->device);
     cudaFree(m->d_kmers);
-    cudaFree(m->d_bub);
-    cudaFree(m->d_back);
+    cudaFree(m->d_in_off);
+    cudaFree(m->d_in_src);
+    cudaFree(m->d_arc_cyc);
+    cudaFree(m->d_scratch);
     cudaFree(m->d_w);
     cudaFree(m->d_m);
     cudaFree(m->d_v);
@@ -448,8 +706,9 @@ int gwfa_model_features_device(gwfa_model *m, uint32_t n, const uint32_t *d_word
     int st = cstat(cudaSetDevice(m->g->device));
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;   // NULL = the legacy default stream
-    const uint32_t blocks = std::min<uint32_t>((n + 7) / 8, 65535);
-    features_kernel<<<blocks, 256, 0, s>>>(m->fg, n, d_words, d_q_off, d_v_s, d_v_e, d_feat);
+    // kFeatWarps warps (8 per CTA), each with its own search tables in d_scratch
+    const uint32_t blocks = std::min<uint32_t>((n + 7) / 8, kFeatWarps / 8);
+    features_kernel<<<blocks, 256, 0, s>>>(m->fg, n, d_words, d_q_off, d_v_s, d_v_e, d_feat, m->d_scratch);
     return cstat(cudaGetLastError());
 }
 
@@ -567,12 +826,11 @@ int gwfa_model_predict_host(const gwfa_model *m, const char *q, uint32_t n, uint
             miss += std::binary_search(m->h_kmers.begin(), m->h_kmers.end(), key) ? 0 : 1;
         }
     }
-    const uint32_t lo = std::min(v_s, v_e), hi = std::max(v_s, v_e);
+    uint32_t sub[4];
+    coreachable_counts(m, v_s, v_e, n, sub);
     const float f[F] = {std::log1p((float)n), n >= (uint32_t)K ? (float)miss / SAMPLES : 0.f,
-                        std::log1p((float)(hi - lo + 1)),
-                        std::log1p((float)(m->g->h_arc_off[hi + 1] - m->g->h_arc_off[lo])),
-                        (float)(m->h_bub[hi + 1] - m->h_bub[lo]) * 1000.f / (float)std::max(n, 1u),
-                        std::log1p((float)(m->h_back[hi + 1] - m->h_back[lo]))};
+                        std::log1p((float)sub[0]), std::log1p((float)sub[1]),
+                        (float)sub[2] * 1000.f / (float)std::max(n, 1u), std::log1p((float)sub[3])};
     const float *w = m->h_w.data();
     float x[F], h1[H], h2[H];
     for (int i = 0; i < F; ++i) x[i] = (f[i] - m->norm.fmean[i]) / m->norm.fstd[i];

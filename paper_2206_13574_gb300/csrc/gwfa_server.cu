@@ -146,10 +146,12 @@ int gwfa_server_default_config(const gwfa_graph *g, gwfa_server_config *c) {
     if (cudaSetDevice(g->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
         return GWFA_ERR_CUDA;
+    // 512-thread CTAs, four per SM; half an SM's worth of them hold large slabs
+    // (and serve small requests when no large one waits)
     c->threads = 512;
-    c->ctas_small = (uint32_t)sms * 4 - (uint32_t)std::max(sms / 8, 1);
-    c->ctas_big = (uint32_t)std::max(sms / 8, 1);
-    c->log2_small = 16;
+    c->ctas_big = (uint32_t)std::max(sms / 2, 1);
+    c->ctas_small = (uint32_t)sms * 4 - c->ctas_big;
+    c->log2_small = 17;
     c->log2_big = 21;
     c->ring_slots = 4096;
     c->max_query_len = 131072;

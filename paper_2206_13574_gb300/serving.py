@@ -15,10 +15,18 @@ import time
 import numpy as np
 
 
-def _summary(lat: np.ndarray, bases: int, wall: float, n: int) -> dict:
-    return {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-            "throughput_qps": n / wall, "gbp_per_s": bases / wall / 1e9, "wall_s": wall}
+def _summary(lat: np.ndarray, bases: int, wall: float, n: int, done_at=None, arrivals=None) -> dict:
+    out = {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+           "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+           "throughput_qps": n / wall, "gbp_per_s": bases / wall / 1e9, "wall_s": wall}
+    if done_at is not None and n > 1:
+        # the rate at which requests completed while they were still arriving: unlike
+        # n / wall it is not set by the drain of the slowest requests after the last
+        # arrival, so it tracks the offered rate until the server saturates
+        window = float(arrivals[n - 1])
+        out["sustained_qps"] = float((done_at <= window).sum()) / window if window > 0 else None
+        out["window_s"] = window
+    return out
 
 
 def run_server(server, queries, arrivals: np.ndarray, idx=None) -> tuple[dict, list]:
@@ -59,7 +67,7 @@ def run_server(server, queries, arrivals: np.ndarray, idx=None) -> tuple[dict, l
     lat = done_at - arrivals[:n]
     bases = int(sum(len(q) for q in qb))
     results = [{f: int(out[i][f]) for f in RESULT_DTYPE.names} for i in range(n)]
-    return _summary(lat, bases, wall, n), results
+    return _summary(lat, bases, wall, n, done_at, arrivals), results
 
 
 def run_plain(graph, queries, arrivals: np.ndarray, idx=None, max_lag: int = 0) -> tuple[dict, list]:

@@ -23,6 +23,47 @@ def _kmer(codes: np.ndarray, p: int) -> int:
     return int(sum(int(codes[p + t]) << (2 * t) for t in range(K)))
 
 
+def coreachable_counts(g, vs: int, ve: int, n: int):
+    """|S|, arcs inside S, vertices with >= 2 arcs inside S, arcs inside S on a cycle:
+    S = vertices v with f(v) + |v| + b(v) <= ceil(1.25 n) + 64, f / b the shortest
+    spelled lengths from v_s up to v / from after v to the end of v_e (Dijkstra)."""
+    import heapq
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    budget = (5 * n + 3) // 4 + 64
+    lens = g.lengths()
+    arcs = np.unique(np.stack([g.arc_src.astype(np.int64), g.arc_dst.astype(np.int64)], 1), axis=0)
+    out_adj, in_adj = {}, {}
+    for u, w in arcs.tolist():
+        out_adj.setdefault(u, []).append(w)
+        in_adj.setdefault(w, []).append(u)
+
+    def search(src, adj):
+        dist = {src: 0}
+        heap = [(0, src)]
+        while heap:
+            d, v = heapq.heappop(heap)
+            if d > dist[v]:
+                continue
+            c = d + int(lens[v])
+            if c > budget:
+                continue
+            for u in adj.get(v, []):
+                if c < dist.get(u, budget + 1):
+                    dist[u] = c
+                    heapq.heappush(heap, (c, u))
+        return dist
+
+    f, b = search(vs, out_adj), search(ve, in_adj)
+    S = {v for v in f if v in b and f[v] + int(lens[v]) + b[v] <= budget}
+    nv = g.n_vertices
+    m = csr_matrix((np.ones(len(arcs)), (arcs[:, 0], arcs[:, 1])), shape=(nv, nv))
+    _, comp = connected_components(m, directed=True, connection="strong")
+    inside = [(u, w) for u, w in arcs.tolist() if u in S and w in S]
+    deg = np.bincount([u for u, _ in inside], minlength=nv) if inside else np.zeros(nv, np.int64)
+    return len(S), len(inside), int((deg >= 2).sum()), sum(int(comp[u] == comp[w]) for u, w in inside)
+
+
 def cpu_features(g, qs) -> np.ndarray:
     """The six raw features, computed the plain way."""
     kset = set()
@@ -30,8 +71,6 @@ def cpu_features(g, qs) -> np.ndarray:
         c = _codes(g.label(v))
         for p in range(len(c) - K + 1):
             kset.add(_kmer(c, p))
-    lens = g.lengths()
-    outdeg = np.bincount(g.arc_src, minlength=g.n_vertices)
     out = np.zeros((len(qs), 6), dtype=np.float64)
     for i in range(len(qs)):
         q = _codes(qs.query(i))
@@ -40,12 +79,24 @@ def cpu_features(g, qs) -> np.ndarray:
         if n >= K:
             for t in range(64):
                 miss += _kmer(q, t * (n - K) // 63) not in kset
-        lo, hi = sorted((int(qs.v_s[i]), int(qs.v_e[i])))
-        sel = (g.arc_src >= lo) & (g.arc_src <= hi)
-        out[i] = [np.log1p(n), miss / 64 if n >= K else 0.0, np.log1p(hi - lo + 1), np.log1p(sel.sum()),
-                  (outdeg[lo:hi + 1] > 1).sum() * 1000.0 / max(n, 1),
-                  np.log1p((sel & (g.arc_dst <= g.arc_src)).sum())]
+        nverts, narcs, nbub, ncyc = coreachable_counts(g, int(qs.v_s[i]), int(qs.v_e[i]), n)
+        out[i] = [np.log1p(n), miss / 64 if n >= K else 0.0, np.log1p(nverts), np.log1p(narcs),
+                  nbub * 1000.0 / max(n, 1), np.log1p(ncyc)]
     return out
+
+
+def shuffled_ids(g, qs, seed: int):
+    """The same graph and queries with vertex ids permuted (ids no longer follow a
+    topological order); every distance is unchanged."""
+    r = np.random.default_rng(seed)
+    perm = r.permutation(g.n_vertices)          # new id of old vertex v
+    inv = np.argsort(perm)                      # old id of new vertex
+    labels = [g.label(int(inv[v])) for v in range(g.n_vertices)]
+    arcs = sorted(set(zip(perm[g.arc_src].tolist(), perm[g.arc_dst].tolist())))
+    g2 = synth.Graph.from_lists(labels, arcs)
+    q2 = synth.Queries(seq=qs.seq, off=qs.off, v_s=perm[qs.v_s].astype(np.uint32),
+                       v_e=perm[qs.v_e].astype(np.uint32), edits=qs.edits, divergence=qs.divergence)
+    return g2, q2
 
 
 # ------------------------------------------------------------------ CPU pins
@@ -108,6 +159,24 @@ def test_features_match_cpu(c2small):
     ref = cpu_features(g, sub)
     assert np.array_equal(f[:, 1], ref[:, 1].astype(np.float32).astype(np.float64))   # k-mer misses exact
     assert np.allclose(f, ref, rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.gpu
+def test_features_on_shuffled_ids_follow_the_subgraph_not_the_ids():
+    """With vertex ids permuted, the id interval [v_s, v_e] no longer describes the
+    s -> e subgraph; the co-reachable counts do not depend on the ids at all."""
+    g0, q0 = synth.make_config(3, n_queries=40, backbone=120_000)   # cyclic: loops count
+    g, qs = shuffled_ids(g0, q0, seed=5)
+    m = gw.CostModel(gw.Graph.from_synth(g))
+    f = m.features(gw.DeviceBatch(qs)).cpu().numpy().astype(np.float64)
+    ref = cpu_features(g, qs)
+    assert np.allclose(f, ref, rtol=1e-5, atol=1e-5)
+    m0 = gw.CostModel(gw.Graph.from_synth(g0))
+    f0 = m0.features(gw.DeviceBatch(q0)).cpu().numpy().astype(np.float64)
+    assert np.array_equal(f0, f)                    # the same subgraphs under either numbering
+    span = np.abs(qs.v_e.astype(np.int64) - qs.v_s.astype(np.int64)) + 1
+    assert (np.log1p(span) != ref[:, 2]).mean() > 0.9   # what the id interval would have counted
+    assert ref[:, 5].max() > 0                          # loop arcs found
 
 
 @pytest.mark.gpu

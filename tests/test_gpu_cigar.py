@@ -124,7 +124,9 @@ def test_capacity_limits_are_reported():
     ops, small = cigars(graph, b, paths, plen, cigar_cap=4096, workspace_bytes=256 << 10)
     d = res["edit_distance"].astype(np.int64)
     m = full["walk_len"].astype(np.int64)
-    need = ((m // 16 + 2) * 4 + 15) // 16 * 16 + (d + 1) ** 2 * 4
+    c = np.ceil(np.sqrt(d + 1)).astype(np.int64)   # checkpoint spacing
+    c = np.where(c * c < d + 1, c + 1, c)
+    need = ((m // 16 + 2) * 4 + 15) // 16 * 16 + (d // c + c + 2) * (2 * d + 1) * 4
     fits = need <= (256 << 10)
     assert fits.any() and (~fits).any()
     assert np.all(small["status"][~fits] == gw.GWFA_ERR_CAPACITY)
@@ -183,3 +185,31 @@ def test_formulation_variants(ends):
         assert c["walk_begin"] <= (first if ends & 1 else 0)
         assert c["walk_end"] >= (len(t) - last if ends & 6 else len(t)) and c["walk_end"] <= len(t)
         assert apply_cigar(qs.query(i), t[c["walk_begin"]:c["walk_end"]], ops[i, :c["n_ops"]]) == c["cost"]
+
+
+def test_large_distances_config4_style():
+    """Distances of thousands (the large workload's 5-10% divergence on tens of kb):
+    the checkpointed backtrace keeps about 2 sqrt(d) wavefronts, so these fit the
+    default 32 MiB per CTA; every CIGAR is valid, costs the Gwfa distance, and equals
+    the oracle's Levenshtein distance of the query and the spelled walk."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    g, q0 = synth.make_config(4, n_queries=600, backbone=3_000_000)
+    L0 = q0.lengths()
+    mid = np.nonzero((q0.divergence > 0.05) & (L0 > 15_000) & (L0 < 45_000))[0][:5]
+    far = np.nonzero((q0.divergence > 0.08) & (L0 > 60_000) & (L0 < 100_000))[0][:1]   # d ~ 6,000
+    pick = np.concatenate([mid, far])
+    assert len(pick) >= 5
+    qs = q0.subset(pick)
+    graph = gw.Graph.from_synth(g)
+    cap = 16384
+    eng, b, paths, plen = traceback_batch(graph, qs, path_cap=cap)
+    res = b.results()
+    assert res["edit_distance"].max() > 5000
+    ops, cr = cigars(graph, b, paths, plen, path_cap=cap, cigar_cap=32768)
+    P = paths.view(len(qs), -1).cpu().numpy()
+    L = plen.cpu().numpy()
+    check_batch(g, qs, res, P, L, ops, cr)
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        lev = list(ex.map(lambda i: oracle.levenshtein(qs.query(i), spelled(g, P[i, :L[i]])), range(len(qs))))
+    assert lev == [int(x) for x in cr["cost"]]
