@@ -462,6 +462,15 @@ class CostModel:
                "gwfa_model_train_device")
         return losses
 
+    def predict_host(self, q: bytes, v_s: int, v_e: int) -> np.ndarray:
+        """The four predictions for one ASCII query, evaluated on the host in fp32
+        (gwfa_model_predict_host: the server's admission path)."""
+        out = np.zeros(MODEL_TARGETS, dtype=np.float32)
+        qb = bytes(q)
+        _check(load().gwfa_model_predict_host(self.handle, qb, len(qb), v_s, v_e, out.ctypes.data),
+               "gwfa_model_predict_host")
+        return out
+
     def save(self, path: str):
         """Weights and normalisation to a file (gwfa_model_save)."""
         _check(load().gwfa_model_save(self.handle, os.fsencode(path)), "gwfa_model_save")

@@ -81,10 +81,10 @@ def _sweep(graph: Graph, batch: DeviceBatch, shapes, max_lag: int, reps: int, pr
     return trials
 
 
-def autotune(graph: Graph, sample, max_lag: int = 0, threads=(32, 64, 128, 256, 512, 1024),
-             per_sm_frac=(0.5, 1.0), log2_tiles=(15, 16), reps: int = 2,
+def autotune(graph: Graph, sample, max_lag: int = 0, threads=(32, 64, 128, 256, 384, 512, 768, 1024),
+             per_sm_frac=(1.0,), log2_tiles=(15, 16), reps: int = 2,
              cache_path: str | None = DEFAULT_CACHE, force: bool = False, final_sample=None,
-             keep: int = 4, max_tier0_bytes: int = 32 << 30) -> dict:
+             keep: int = 5, max_tier0_bytes: int = 32 << 30) -> dict:
     """Best {threads, ctas, log2_tiles} for `graph` from a timing sweep.
 
     Stage 1 times every shape on `sample`; with `final_sample` (a held-out batch of
@@ -92,7 +92,9 @@ def autotune(graph: Graph, sample, max_lag: int = 0, threads=(32, 64, 128, 256, 
     full batch by throughput, and the best shape differs) the best shape of each CTA
     width within 4x of the fastest (at most `keep` widths) is timed again on it with
     `reps` repetitions and the best of those is chosen.
-    Shapes whose tier-0 slabs would exceed max_tier0_bytes are skipped."""
+    Shapes whose tier-0 slabs would exceed max_tier0_bytes are skipped.  By default
+    every shape fills the GPU (per_sm_frac 1.0): a persistent batch is bound by
+    throughput, and a small sample cannot tell a half-filled GPU from a full one."""
     import torch
     prune = max_lag > 0
     key = fingerprint(graph, prune)

@@ -1205,15 +1205,17 @@ __global__ void fill_kernel(uint4 *p, uint64_t n16) {
 }
 
 // Slabs start empty: slot keys and offsets all ones (empty / absent), lane-mask
-// words 0 (the second 8 bytes of every slot); the lists need no initial value.
+// words 0 (the second 8 bytes of every slot).  Only the hash slots are written:
+// every list of the slab (touched, Q, spills, frontier snapshots, spill requests,
+// T) is written before it is read.
 __global__ void slab_init_kernel(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_slabs,
                                  uint64_t slots_bytes, uint64_t slot_bytes) {
-    const uint64_t per = slab_bytes / 16, total = per * n_slabs;
+    const uint64_t per = slots_bytes / 16, total = per * n_slabs;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t o = (i % per) * 16;
-        const bool head = o < slots_bytes && o % slot_bytes == 0;
-        ((uint4 *)slabs)[i] = head ? make_uint4(~0u, ~0u, 0u, 0u) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        const uint64_t o = (i % per) * 16;   // offset inside the slab's slot region
+        uint4 *p = (uint4 *)(slabs + (i / per) * slab_bytes + o);
+        *p = o % slot_bytes == 0 ? make_uint4(~0u, ~0u, 0u, 0u) : make_uint4(~0u, ~0u, ~0u, ~0u);
     }
 }
 
@@ -1264,7 +1266,7 @@ cudaError_t launch_fill(void *p, uint64_t bytes, cudaStream_t st) {
 cudaError_t launch_slab_init(uint8_t *slabs, uint64_t slab_bytes, uint32_t n_slabs, uint32_t log2cap,
                              bool prune, cudaStream_t st) {
     const SlabLayout L = slab_layout(log2cap, prune);
-    const uint64_t n16 = slab_bytes / 16 * n_slabs;
+    const uint64_t n16 = (L.touched - L.slots) / 16 * n_slabs;
     if (n16 == 0) return cudaSuccess;
     uint64_t blocks = (n16 + 255) / 256;
     if (blocks > 8192) blocks = 8192;

@@ -459,45 +459,89 @@ static std::vector<uint32_t> strong_components(uint32_t nv, const std::vector<ui
     return comp;
 }
 
+// vertex -> spelled length, open addressing (the host searches run once per served
+// request, so they avoid node allocation)
+struct DistMap {
+    std::vector<uint32_t> key;
+    std::vector<uint64_t> val;
+    uint32_t mask = 0, size = 0;
+    static constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+    DistMap() : key(1024, kEmpty), val(1024, 0), mask(1023) {}
+    uint32_t slot(uint32_t v) const {
+        uint32_t h = (v * 0x9E3779B1u) & mask;
+        while (key[h] != kEmpty && key[h] != v) h = (h + 1) & mask;
+        return h;
+    }
+    const uint64_t *find(uint32_t v) const {
+        const uint32_t h = slot(v);
+        return key[h] == v ? &val[h] : nullptr;
+    }
+    // sets v's length to d if absent or larger; true if it changed
+    bool lower(uint32_t v, uint64_t d) {
+        uint32_t h = slot(v);
+        if (key[h] == v) {
+            if (d >= val[h]) return false;
+            val[h] = d;
+            return true;
+        }
+        if (2 * (size + 1) > mask + 1) {   // keep the load at most one half
+            std::vector<uint32_t> k2;
+            std::vector<uint64_t> v2;
+            k2.swap(key);
+            v2.swap(val);
+            key.assign(2 * k2.size(), kEmpty);
+            val.assign(2 * k2.size(), 0);
+            mask = (uint32_t)key.size() - 1;
+            for (size_t i = 0; i < k2.size(); ++i)
+                if (k2[i] != kEmpty) {
+                    const uint32_t s2 = slot(k2[i]);
+                    key[s2] = k2[i];
+                    val[s2] = v2[i];
+                }
+            h = slot(v);
+        }
+        key[h] = v;
+        val[h] = d;
+        ++size;
+        return true;
+    }
+};
+
 // The co-reachable subgraph counts of the features kernel, on the host (serving
 // admission): |S|, arcs inside S, vertices with two or more of them, cycle arcs.
 static void coreachable_counts(const gwfa_model *m, uint32_t vs, uint32_t ve, uint64_t n, uint32_t out[4]) {
     const gwfa_graph *g = m->g;
     const uint64_t budget = (5 * n + 3) / 4 + 64;
     auto len = [&](uint32_t v) { return (uint64_t)(g->h_vlen[v]); };
-    auto search = [&](uint32_t src, bool fwd) {
-        std::unordered_map<uint32_t, uint64_t> dist;
+    auto search = [&](uint32_t src, bool fwd, DistMap &dist) {
         std::vector<uint32_t> cur{src}, nxt;
-        dist[src] = 0;
+        dist.lower(src, 0);
         while (!cur.empty()) {
             nxt.clear();
             for (uint32_t v : cur) {
-                const uint64_t c = dist[v] + len(v);
+                const uint64_t c = *dist.find(v) + len(v);
                 if (c > budget) continue;
                 const uint32_t a0 = fwd ? g->h_arc_off[v] : m->h_in_off[v];
                 const uint32_t a1 = fwd ? g->h_arc_off[v + 1] : m->h_in_off[v + 1];
                 for (uint32_t a = a0; a < a1; ++a) {
                     const uint32_t u = fwd ? g->h_arc_dst[a] : m->h_in_src[a];
-                    auto it = dist.find(u);
-                    if (it == dist.end() || c < it->second) {
-                        dist[u] = c;
-                        nxt.push_back(u);
-                    }
+                    if (dist.lower(u, c)) nxt.push_back(u);
                 }
             }
             std::swap(cur, nxt);
         }
-        return dist;
     };
-    const auto f = search(vs, true), b = search(ve, false);
+    DistMap f, b;
+    search(vs, true, f);
+    search(ve, false, b);
     auto in_s = [&](uint32_t v) {
-        auto i = f.find(v), j = b.find(v);
-        return i != f.end() && j != b.end() && i->second + len(v) + j->second <= budget;
+        const uint64_t *i = f.find(v), *j = b.find(v);
+        return i && j && *i + len(v) + *j <= budget;
     };
     uint32_t nverts = 0, narcs = 0, nbub = 0, ncyc = 0;
-    for (const auto &kv : f) {
-        const uint32_t v = kv.first;
-        if (!in_s(v)) continue;
+    for (size_t x = 0; x < f.key.size(); ++x) {
+        const uint32_t v = f.key[x];
+        if (v == DistMap::kEmpty || !in_s(v)) continue;
         ++nverts;
         uint32_t deg = 0;
         for (uint32_t a = g->h_arc_off[v]; a < g->h_arc_off[v + 1]; ++a) {

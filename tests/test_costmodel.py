@@ -215,6 +215,13 @@ def test_training_learns_work_counts(c2small):
     pred = m.predict(tf).cpu().numpy()
     r2 = costmodel.r2(pred, tt.cpu().numpy())
     assert r2[0] > 0.6 and r2[3] > 0.6, r2         # distance and work on held-out queries
+    # the host evaluation (serving admission: host features, fp32 forward) agrees with
+    # the device's (fp16 weights and activations) on held-out queries
+    held = qs.subset(np.arange(400, 600))
+    pall = m.predict(m.features(gw.DeviceBatch(held))).cpu().numpy()
+    for i in range(0, 200, 10):
+        h = m.predict_host(held.query(i), int(held.v_s[i]), int(held.v_e[i]))
+        assert np.all(np.abs(h - pall[i]) <= 0.05 + 0.02 * np.abs(pall[i])), (i, h, pall[i])
     # the trained model through a file (gwfa_model_save / gwfa_model_load) predicts the same
     import tempfile
     path = os.path.join(tempfile.mkdtemp(), "model.bin")

@@ -7,7 +7,8 @@ compared, element by element, with the oracle's Alg. 1-4 (Sec. 2.4-2.5; the exac
 distances are Eq. 1's, to which exact Gwfa is pinned elsewhere):
 
 * cyclic graph, lag-pruned with a_diff = 1000 (Alg. 4): 200 queries;
-* cyclic graph, exact: 16 queries (each costs the oracle ~60 M cells);
+* cyclic graph, exact: 16 queries (each costs the oracle ~60 M cells), four of them
+  also against Eq. 1's DP;
 * cyclic graph, lag-pruned with the memory bound on H~ at the same lag: 100 queries;
 * 50 Mb graph, exact: ~200 queries stratified over the whole divergence range and
   chosen within an oracle cell budget (estimated from the generator's injected edit
@@ -87,6 +88,9 @@ def test_config3_exact_sample_and_upper_bound(c3):
     want = oracle.gwfa_many(ga, sub, range(len(sub)))
     for i, w in enumerate(want):
         same(res[i], w, ("exact", int(idx[i])))
+    # and the definition itself (Eq. 1's DP over the co-reachable subgraph) on four
+    dp = oracle.dp_many(ga, sub, range(4))
+    assert [int(x) for x in res["edit_distance"][:4]] == dp
     eng.close()
     peng = gw.Engine(graph, prune=True)
     pr = peng.align_batch(sub.seq, sub.off, sub.v_s, sub.v_e, max_lag=1000)
