@@ -267,7 +267,7 @@ if __name__ == "__main__":
     t0 = time.time()
     res = {"config3": config3, "scheduler": scheduler, "serving": serving,
            "scheduler100k": lambda: scheduler(n=100_000, n_plain=0, only=("plain_fifo", "learned")),
-           "serving5": lambda: serving(n_pool=2000, rates=(250.0, 1000.0, 4000.0), duration=1.0,
+           "serving5": lambda: serving(n_pool=3000, rates=(1000.0, 2000.0, 5000.0, 10000.0), duration=4.0,
                                        plain_rate=10.0, plain_duration=3.0, cfg=5, with_model=True)}[which]()
     res["wall_s"] = time.time() - t0
     print(json.dumps(res))
