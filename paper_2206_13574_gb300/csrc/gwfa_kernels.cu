@@ -46,6 +46,8 @@ namespace {
 constexpr long long kTagPend = 0, kTagFresh = 1, kTagSettled = 2;
 constexpr uint32_t kBaseMask = 0x3FFFFFFFu;
 constexpr int kStack = 6;   // depth-first spill stack per thread (exact mode)
+constexpr int kExtendTiles = 2;   // tiles an 8-lane group extends together (exact mode)
+constexpr int kExpandTiles = 2;   // frontier entries a group expands together
 constexpr uint32_t kNoTrace = 0x3FFFFFFFu;   // trace index of the start diagonal (no predecessor)
 
 template <bool P> struct VT;
@@ -108,6 +110,10 @@ struct Sh {
     uint32_t claim[3];  // work counters of the phases, rotating (see align_one)
     uint32_t tlen;      // traceback: entries of T
     unsigned long long end_vp;   // traceback: vertex << 32 | trace of a diagonal at the end point
+    unsigned long long t_start;  // query start (global timer, ns)
+    unsigned long long t_phase;  // statistics: start of the current phase
+    unsigned long long st[6];    // statistics: extend ns, expand ns, rounds, extended tiles,
+                                 // expanded tiles, largest extended frontier (thread 0 only)
 };
 
 __device__ __forceinline__ void set_err(Sh &sh, int code) { atomicCAS(&sh.err, 0, code); }
@@ -315,43 +321,47 @@ __device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const
     }
 }
 
-// One extension round over `list` in exact mode.  Each 8-lane group takes two
-// tiles per iteration and keeps both dependency chains (list entry -> mask,
-// offsets, vertex info -> first LCP window) in flight together.
+// One extension round over `list` in exact mode.  Each 8-lane group takes
+// kExtendTiles tiles per iteration and keeps their dependency chains (list entry ->
+// mask, offsets, vertex info -> first LCP window) in flight together.
 __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &sh, const QCtx &q,
                                    const LEnt *list, uint32_t n_list, int par, int next_par,
                                    LEnt *next_list, uint32_t *next_count, uint32_t *claim) {
+    constexpr int U = kExtendTiles;
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     for (;;) {
-        const uint32_t e0 = group_claim(claim, 2u, gmask, ln);
+        const uint32_t e0 = group_claim(claim, (uint32_t)U, gmask, ln);
         if (e0 >= n_list) break;
-        const bool has1 = e0 + 1 < n_list;   // uniform within the group
-        LEnt ent[2];
-        ent[0] = ld_lent(&list[e0]);
-        ent[1] = has1 ? ld_lent(&list[e0 + 1]) : ent[0];
-        uint32_t m[2] = {0u, 0u};
-        int val[2];
-        uint4 vi[2];
+        const uint32_t cnt = min((uint32_t)U, n_list - e0);   // uniform within the group
+        LEnt ent[U];
+        uint32_t m[U];
+        int val[U];
+        uint2 vi[U];   // label word, |v| (the arc range is reloaded for the rare spill)
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (ln == 0 && (u == 0 || has1)) m[u] = atomicExch(&s.slots[ent[u].slot].reg[par], 0u);
+        for (int u = 0; u < U; ++u) {
+            ent[u] = (u == 0 || (uint32_t)u < cnt) ? ld_lent(&list[e0 + u]) : ent[0];
+            m[u] = 0u;
+            if (ln == 0 && (uint32_t)u < cnt) m[u] = atomicExch(&s.slots[ent[u].slot].reg[par], 0u);
             val[u] = __ldcg(&s.slots[ent[u].slot].vals[ln]);
-            vi[u] = __ldg(&g.vinfo[ent[u].v]);
+            vi[u] = __ldg((const uint2 *)&g.vinfo[ent[u].v]);
         }
-        uint32_t eidx = 0;
-        m[0] = __shfl_sync(gmask, m[0], 0, 8);
-        m[1] = __shfl_sync(gmask, m[1], 0, 8);
+        uint32_t eidx = 0, pop = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            m[u] = __shfl_sync(gmask, m[u], 0, 8);
+            pop += __popc(m[u]);
+        }
         if (ln == 0) {
-            eidx = atomicAdd(&sh.ne, has1 ? 2u : 1u);
-            atomicAdd(&sh.score_cells, (uint32_t)(__popc(m[0]) + __popc(m[1])));
+            eidx = atomicAdd(&sh.ne, cnt);
+            atomicAdd(&sh.score_cells, pop);
         }
         eidx = __shfl_sync(gmask, eidx, 0, 8);
-        bool live[2];
-        int k[2], maxl[2];
-        uint32_t x[2];
+        bool live[U];
+        int k[U], maxl[U];
+        uint32_t x[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             live[u] = (m[u] >> ln) & 1u;
             k[u] = ent[u].kb * kTile + ln;
             maxl[u] = 0;
@@ -364,8 +374,8 @@ __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (u == 1 && !has1) break;
+        for (int u = 0; u < U; ++u) {
+            if ((uint32_t)u >= cnt) break;
             if (live[u]) {
                 val[u] += lcp_finish(q, k[u] + val[u], g.words + vi[u].x, val[u], maxl[u], x[u]);
                 __stcg(&s.slots[ent[u].slot].vals[ln], val[u]);
@@ -380,11 +390,12 @@ __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (u == 1 && !has1) break;
-            if (live[u] && (uint32_t)val[u] == vi[u].y)
-                spill_dfs(g, s, sh, q, vi[u].z, vi[u].w, k[u] + (int)vi[u].y, next_par, next_list,
-                          next_count);
+        for (int u = 0; u < U; ++u) {
+            if ((uint32_t)u >= cnt) break;
+            if (live[u] && (uint32_t)val[u] == vi[u].y) {
+                const uint4 full = __ldg(&g.vinfo[ent[u].v]);
+                spill_dfs(g, s, sh, q, full.z, full.w, k[u] + (int)vi[u].y, next_par, next_list, next_count);
+            }
         }
     }
 }
@@ -419,7 +430,7 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
         uint32_t m = 0, eidx = 0;
         if (ln == 0) m = atomicExch(&s.slots[ent.slot].reg[par], 0u);
         long long val = __ldcg(&s.slots[ent.slot].vals[ln]);
-        const uint4 vi = __ldg(&g.vinfo[ent.v]);
+        const uint2 vi = __ldg((const uint2 *)&g.vinfo[ent.v]);   // label word, |v|
         const uint32_t tr = traceback ? __ldcg(&s.slots[ent.slot].trace[ln]) : 0u;
         m = __shfl_sync(gmask, m, 0, 8);
         if (ln == 0) {
@@ -451,7 +462,8 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
                 const uint32_t t = traceback ? push_trace(s, sh, ent.v, tr) : 0u;
                 const uint32_t r = atomicAdd(req_count, 1u);
                 if (r < s.cap) {
-                    __stcg(&s.req[r], make_int4(k + (int)vi.y, (int)nb, (int)vi.z, (int)vi.w));
+                    const uint4 full = __ldg(&g.vinfo[ent.v]);   // the arc range, for the rare spill
+                    __stcg(&s.req[r], make_int4(k + (int)vi.y, (int)nb, (int)full.z, (int)full.w));
                     if (traceback) __stcg(&s.reqt[r], t);
                 } else {
                     set_err(sh, GWFA_ERR_CAPACITY);
@@ -540,8 +552,8 @@ __device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, u
 }
 
 // GwfExpand (Alg. 3) over the extended frontier, with GwfPrune (Alg. 4) applied
-// to the sources on the way in.  Two snapshot entries per group and iteration:
-// their candidate max-merges are issued together before either registration.
+// to the sources on the way in.  kExpandTiles snapshot entries per group and
+// iteration: their candidate max-merges are issued together before any registration.
 template <bool P>
 __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e, bool prune_on,
                            long long amax, int max_lag, int par, uint32_t *qcount, uint32_t *claim,
@@ -549,15 +561,16 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
     using T = typename VT<P>::T;
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
+    constexpr int U = kExpandTiles;
     const uint32_t ne = min(n_e, s.cap);
     for (;;) {
-        const uint32_t base = group_claim(claim, 2u, gmask, ln);
+        const uint32_t base = group_claim(claim, (uint32_t)U, gmask, ln);
         if (base >= ne) break;
-        bool valid[2], ins[2], del[2];
-        EHdr h[2];
-        T c_ins[2], c_del[2], cand[2], prev[2];
+        bool valid[U], ins[U], del[U];
+        EHdr h[U];
+        T c_ins[U], c_del[U], cand[U], prev[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const uint32_t e = base + u;
             valid[u] = e < ne;
             h[u] = EHdr{0u, 0u, 0, 0u};
@@ -601,13 +614,13 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
             if (from_right > cand[u]) cand[u] = from_right;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             prev[u] = (T)0x7FFFFFFF;
             if (valid[u] && cand[u] >= 0)
                 prev[u] = atomicMax(&s.slots[h[u].slot_mask & 0xFFFFFFu].vals[ln], cand[u]);
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             if (!(valid[u] && cand[u] >= 0)) continue;
             if (prev[u] < 0) atomicAdd(&sh.visited, 1ull);
             if constexpr (P) {
@@ -620,7 +633,7 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
                            h[u].kb, 1u << ln, sh);
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             if (valid[u] && ln == 7 && ins[u]) {   // insertion leaves the tile: (v, 8(kb+1))
                 const int t = find_or_insert(s, sh, tile_key(h[u].v, h[u].kb + 1));
                 if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb + 1, 0, c_ins[u], par, qcount, traceback);
@@ -787,10 +800,10 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         return;
     }
     q.ke = n - (int)__ldg(&g.vinfo[q.ve]).y;
-    const unsigned long long t_start = globaltimer_ns();
-
     // Alg. 1 initialisation: H~_{v_s,0} <- 0, Q <- [(v_s, 0)], d <- 0
     if (threadIdx.x == 0) {
+        sh.t_start = globaltimer_ns();
+        for (int i = 0; i < 6; ++i) sh.st[i] = 0;
         sh.err = 0;
         sh.nt = 0;
         sh.cells = sh.visited = sh.pruned = sh.spills = sh.evicted = 0;
@@ -847,9 +860,6 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
     int d = 0;
     int status = 0;
     int failed = 0;
-    // optional per-query statistics (thread 0): extend / expand time, rounds, tiles
-    unsigned long long st_ext = 0, st_exp = 0, st_rounds = 0, st_ext_tiles = 0, st_exp_tiles = 0,
-                       st_max_tiles = 0;
     for (;;) {
         // ---- GwfExtend (Alg. 2)
         if (threadIdx.x == 0) {
@@ -864,11 +874,11 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         __syncthreads();
         const LEnt *list = s.qlist;
         uint32_t n_list = min(sh.nq[d & 1], s.cap);
-        const unsigned long long t_ext = A.stats ? globaltimer_ns() : 0;
+        if (A.stats && threadIdx.x == 0) sh.t_phase = globaltimer_ns();
         for (int round = 0;; ++round) {
-            if (A.stats) {
-                st_rounds++;
-                st_ext_tiles += n_list;
+            if (A.stats && threadIdx.x == 0) {
+                sh.st[2]++;
+                sh.st[3] += n_list;
             }
             const uint32_t next_phase = phase + 1;
             LEnt *next_list = s.slist[(round + 1) & 1];
@@ -912,12 +922,12 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             sh.cells += sh.score_cells;
             sh.peak = max(sh.peak, sh.score_cells);
         }
-        unsigned long long t_exp = 0;
-        if (A.stats) {
-            t_exp = globaltimer_ns();
-            st_ext += t_exp - t_ext;
-            st_exp_tiles += sh.ne;
-            st_max_tiles = max(st_max_tiles, (unsigned long long)sh.ne);
+        if (A.stats && threadIdx.x == 0) {
+            const unsigned long long t = globaltimer_ns();
+            sh.st[0] += t - sh.t_phase;
+            sh.t_phase = t;
+            sh.st[4] += sh.ne;
+            sh.st[5] = max(sh.st[5], (unsigned long long)sh.ne);
         }
         if (failed) break;
         // end test of Alg. 1
@@ -949,7 +959,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                 failed = __syncthreads_or(sh.err != 0);
             }
         }
-        if (A.stats) st_exp += globaltimer_ns() - t_exp;
+        if (A.stats && threadIdx.x == 0) sh.st[1] += globaltimer_ns() - sh.t_phase;
         if (failed) break;
         if (sh.nq[d & 1] == 0) {
             status = P && A.max_lag > 0 ? GWFA_ERR_EMPTY_FRONTIER : GWFA_ERR_UNREACHABLE;
@@ -999,16 +1009,11 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                     }
                 }
             }
-            r.device_us = (uint32_t)min((globaltimer_ns() - t_start) / 1000ull, 0xFFFFFFFFull);
+            r.device_us = (uint32_t)min((globaltimer_ns() - sh.t_start) / 1000ull, 0xFFFFFFFFull);
             A.out[qid] = r;
             if (A.stats) {
                 unsigned long long *o = A.stats + (uint64_t)qid * kStatWords;
-                o[0] = st_ext;
-                o[1] = st_exp;
-                o[2] = st_rounds;
-                o[3] = st_ext_tiles;
-                o[4] = st_exp_tiles;
-                o[5] = st_max_tiles;
+                for (int i = 0; i < 6; ++i) o[i] = sh.st[i];
                 o[6] = sh.nt;
                 o[7] = (unsigned long long)(d + 1);
             }
@@ -1022,7 +1027,12 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
 template <bool P>
 __device__ __forceinline__ void align_queries(const TierArgs &A) {
     __shared__ Sh sh;
-    const Slab<P> s = carve<P>(A.slabs + (uint64_t)blockIdx.x * A.slab_bytes, A.log2cap);
+    // the slab's array pointers are the same for every thread: held once in shared
+    // memory rather than in each thread's registers (where, at 32 registers, they
+    // were spilled to local memory and reloaded through L1/L2 in the hot phases);
+    // visible to all threads after the first barrier of the loop below
+    __shared__ Slab<P> s;
+    if (threadIdx.x == 0) s = carve<P>(A.slabs + (uint64_t)blockIdx.x * A.slab_bytes, A.log2cap);
     const uint32_t count = A.list_count ? *A.list_count : A.count_val;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1079,7 +1089,8 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
     const int cls = blockIdx.x < S.n_small ? 0 : 1;
     uint8_t *base = cls == 0 ? S.slabs + (uint64_t)blockIdx.x * S.slab_bytes[0]
                              : S.slabs + S.big_offset + (uint64_t)(blockIdx.x - S.n_small) * S.slab_bytes[1];
-    const Slab<P> s = carve<P>(base, S.log2cap[cls]);
+    __shared__ Slab<P> s;   // as in align_queries; visible after the first poll barrier
+    if (threadIdx.x == 0) s = carve<P>(base, S.log2cap[cls]);
     for (;;) {
         if (threadIdx.x == 0) {
             int go = 0;
