@@ -251,13 +251,15 @@ __device__ __forceinline__ void reg_append(uint32_t *regw, LEnt *list, uint32_t 
     }
 }
 
-// Dynamic work distribution inside a phase: the group's lane 0 claims the next
-// `step` entries, so a group held up by a long exact-match run or spill chain does
-// not stall the others at the phase barrier.
-__device__ __forceinline__ uint32_t group_claim(uint32_t *ctr, uint32_t step, unsigned gmask, int ln) {
+// Dynamic work distribution inside a phase: lane 0 of a warp claims the next
+// 4 x `step` entries for the warp's four groups (group g of the warp takes entries
+// [base + g step, base + (g + 1) step)), so a warp held up by a long exact-match run
+// or spill chain does not stall the others at the phase barrier, and the four groups
+// run the same iterations in step.  Every lane of the warp calls it.
+__device__ __forceinline__ uint32_t warp_claim(uint32_t *ctr, uint32_t step) {
     uint32_t e = 0;
-    if (ln == 0) e = atomicAdd(ctr, step);
-    return __shfl_sync(gmask, e, 0, 8);
+    if ((threadIdx.x & 31) == 0) e = atomicAdd(ctr, 4u * step);
+    return __shfl_sync(0xFFFFFFFFu, e, 0);
 }
 
 
@@ -331,8 +333,10 @@ __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     for (;;) {
-        const uint32_t e0 = group_claim(claim, (uint32_t)U, gmask, ln);
-        if (e0 >= n_list) break;
+        const uint32_t wb = warp_claim(claim, (uint32_t)U);
+        if (wb >= n_list) break;
+        const uint32_t e0 = wb + ((threadIdx.x & 31) >> 3) * (uint32_t)U;
+        if (e0 >= n_list) continue;   // nothing left for this group in the warp's claim
         const uint32_t cnt = min((uint32_t)U, n_list - e0);   // uniform within the group
         LEnt ent[U];
         uint32_t m[U];
@@ -424,8 +428,10 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     for (;;) {
-        const uint32_t e = group_claim(claim, 1u, gmask, ln);
-        if (e >= n_list) break;
+        const uint32_t wb = warp_claim(claim, 1u);
+        if (wb >= n_list) break;
+        const uint32_t e = wb + ((threadIdx.x & 31) >> 3);
+        if (e >= n_list) continue;
         const LEnt ent = ld_lent(&list[e]);
         uint32_t m = 0, eidx = 0;
         if (ln == 0) m = atomicExch(&s.slots[ent.slot].reg[par], 0u);
@@ -536,7 +542,6 @@ __device__ void resolve_spill_traces(const DevGraph &g, const Slab<true> &s, Sh 
 __device__ __forceinline__ bool first_fresh(long long prev, long long cand) {
     return cand > prev && ((prev >> 30) & 3) != kTagFresh;
 }
-__device__ __forceinline__ bool first_fresh(int, int) { return false; }
 
 // Offer value `cand` to lane `ln` of tile (slot, v, kb): GwfExpand's max-merge
 // into H~; the lane joins the next Q if its offset strictly improved.
@@ -564,8 +569,10 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
     constexpr int U = kExpandTiles;
     const uint32_t ne = min(n_e, s.cap);
     for (;;) {
-        const uint32_t base = group_claim(claim, (uint32_t)U, gmask, ln);
-        if (base >= ne) break;
+        const uint32_t wb = warp_claim(claim, (uint32_t)U);
+        if (wb >= ne) break;
+        const uint32_t base = wb + ((threadIdx.x & 31) >> 3) * (uint32_t)U;
+        if (base >= ne) continue;
         bool valid[U], ins[U], del[U];
         EHdr h[U];
         T c_ins[U], c_del[U], cand[U], prev[U];
@@ -657,8 +664,10 @@ __device__ void resolve_expand_traces(const Slab<true> &s, Sh &sh, const QCtx &q
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     const uint32_t ne = min(n_e, s.cap);
     for (;;) {
-        const uint32_t e = group_claim(claim, 1u, gmask, ln);
-        if (e >= ne) break;
+        const uint32_t wb = warp_claim(claim, 1u);
+        if (wb >= ne) break;
+        const uint32_t e = wb + ((threadIdx.x & 31) >> 3);
+        if (e >= ne) continue;
         const EHdr h = ld_ehdr(&s.elist[e].hdr);
         const long long val = __ldcg(&s.elist[e].vals[ln]);
         const uint32_t tr = __ldcg(&s.elist[e].trace[ln]);
