@@ -46,8 +46,10 @@ namespace {
 constexpr long long kTagPend = 0, kTagFresh = 1, kTagSettled = 2;
 constexpr uint32_t kBaseMask = 0x3FFFFFFFu;
 constexpr int kStack = 6;   // depth-first spill stack per thread (exact mode)
-constexpr int kExtendTiles = 2;   // tiles an 8-lane group extends together (exact mode)
-constexpr int kExpandTiles = 2;   // frontier entries a group expands together
+// Tiles an 8-lane group takes per iteration (exact mode; pruning mode expands one):
+// two, kept in flight together, when a phase has at least kWideTiles entries per
+// group, else one.
+constexpr int kWideTiles = 16;
 constexpr uint32_t kNoTrace = 0x3FFFFFFFu;   // trace index of the start diagonal (no predecessor)
 
 template <bool P> struct VT;
@@ -217,11 +219,17 @@ __device__ __forceinline__ unsigned long long tile_key(uint32_t v, int kb) {
     return ((unsigned long long)v << 32) | (uint32_t)kb;
 }
 
+__device__ __forceinline__ uint32_t tile_hash(unsigned long long key, uint32_t mask) {
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & mask;
+}
+
+// find_or_insert's probe sequence when the key of its first slot h was already read
+// (cur), so that the read can be issued ahead of other round trips.
 template <bool P>
-__device__ int find_or_insert(const Slab<P> &s, Sh &sh, unsigned long long key) {
-    uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & s.mask;
+__device__ int find_or_insert_at(const Slab<P> &s, Sh &sh, unsigned long long key, uint32_t h,
+                                 unsigned long long cur) {
     for (int probe = 0; probe < 256; ++probe) {
-        const unsigned long long cur = __ldcg(&s.slots[h].key);
+        if (probe > 0) cur = __ldcg(&s.slots[h].key);
         if (cur == key) return (int)h;
         if (cur == kEmptyKey) {
             const unsigned long long prev = atomicCAS(&s.slots[h].key, kEmptyKey, key);
@@ -237,6 +245,12 @@ __device__ int find_or_insert(const Slab<P> &s, Sh &sh, unsigned long long key) 
     }
     set_err(sh, GWFA_ERR_CAPACITY);
     return -1;
+}
+
+template <bool P>
+__device__ int find_or_insert(const Slab<P> &s, Sh &sh, unsigned long long key) {
+    const uint32_t h = tile_hash(key, s.mask);
+    return find_or_insert_at(s, sh, key, h, __ldcg(&s.slots[h].key));
 }
 
 // Make lane `bit` of tile (slot, v, kb) live for the phase owning `regw`; the
@@ -324,12 +338,12 @@ __device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const
 }
 
 // One extension round over `list` in exact mode.  Each 8-lane group takes
-// kExtendTiles tiles per iteration and keeps their dependency chains (list entry ->
+// U tiles per iteration and keeps their dependency chains (list entry ->
 // mask, offsets, vertex info -> first LCP window) in flight together.
+template <int U>
 __device__ void extend_round_exact(const DevGraph &g, const Slab<false> &s, Sh &sh, const QCtx &q,
                                    const LEnt *list, uint32_t n_list, int par, int next_par,
                                    LEnt *next_list, uint32_t *next_count, uint32_t *claim) {
-    constexpr int U = kExtendTiles;
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     for (;;) {
@@ -557,16 +571,15 @@ __device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, u
 }
 
 // GwfExpand (Alg. 3) over the extended frontier, with GwfPrune (Alg. 4) applied
-// to the sources on the way in.  kExpandTiles snapshot entries per group and
+// to the sources on the way in.  U snapshot entries per group and
 // iteration: their candidate max-merges are issued together before any registration.
-template <bool P>
+template <bool P, int U>
 __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e, bool prune_on,
                            long long amax, int max_lag, int par, uint32_t *qcount, uint32_t *claim,
                            bool traceback) {
     using T = typename VT<P>::T;
     const int ln = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
-    constexpr int U = kExpandTiles;
     const uint32_t ne = min(n_e, s.cap);
     for (;;) {
         const uint32_t wb = warp_claim(claim, (uint32_t)U);
@@ -620,6 +633,17 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
             if (from_left > cand[u]) cand[u] = from_left;
             if (from_right > cand[u]) cand[u] = from_right;
         }
+        // the neighbour tile a boundary lane leaves for (insertion from lane 7, deletion
+        // from lane 0): its first hash read goes out before this tile's merges
+        unsigned long long nkey[U], ncur[U];
+        uint32_t nh[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool out = valid[u] && ((ln == 7 && ins[u]) || (ln == 0 && del[u]));
+            nkey[u] = tile_key(h[u].v, h[u].kb + (ln == 7 ? 1 : -1));
+            nh[u] = tile_hash(nkey[u], s.mask);
+            ncur[u] = out ? __ldcg(&s.slots[nh[u]].key) : 0ull;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             prev[u] = (T)0x7FFFFFFF;
@@ -642,11 +666,11 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (valid[u] && ln == 7 && ins[u]) {   // insertion leaves the tile: (v, 8(kb+1))
-                const int t = find_or_insert(s, sh, tile_key(h[u].v, h[u].kb + 1));
+                const int t = find_or_insert_at(s, sh, nkey[u], nh[u], ncur[u]);
                 if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb + 1, 0, c_ins[u], par, qcount, traceback);
             }
             if (valid[u] && ln == 0 && del[u]) {   // deletion leaves the tile: (v, 8 kb - 1)
-                const int t = find_or_insert(s, sh, tile_key(h[u].v, h[u].kb - 1));
+                const int t = find_or_insert_at(s, sh, nkey[u], nh[u], ncur[u]);
                 if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb - 1, 7, c_del[u], par, qcount, traceback);
             }
         }
@@ -782,7 +806,9 @@ __device__ void evict_behind(const Slab<true> &s, Sh &sh, long long amax, int la
     __syncthreads();
 }
 
-template <bool P>
+// kWide: large phases may take two tiles per group (the batch kernels; the server
+// kernel, whose ring handling holds more registers, takes one).
+template <bool P, bool kWide>
 __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t qid) {
     const DevGraph &g = A.g;
     const uint64_t qo = A.q_off[qid];
@@ -915,8 +941,12 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                     resolve_spill_traces(g, s, sh, sh.nreq[round & 1]);
                 }
             } else {
-                extend_round_exact(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
-                                   next_count, claim);
+                if (kWide && n_list >= kWideTiles * (blockDim.x >> 3))
+                    extend_round_exact<2>(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
+                                          next_count, claim);
+                else
+                    extend_round_exact<1>(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
+                                          next_count, claim);
             }
             // every exit decision comes from a barrier reduction: sh.err may be set by
             // threads that already run the next phase, so it is never re-read for control
@@ -953,8 +983,17 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         }
         uint32_t *claim = &sh.claim[cstep % 3];
         ++cstep;
-        expand_all<P>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
-                      A.traceback != 0);
+        if constexpr (!P) {
+            if (kWide && sh.ne >= kWideTiles * (blockDim.x >> 3))
+                expand_all<P, 2>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
+                                 A.traceback != 0);
+            else
+                expand_all<P, 1>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
+                                 A.traceback != 0);
+        } else {
+            expand_all<P, 1>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
+                             A.traceback != 0);
+        }
         failed = __syncthreads_or(sh.err != 0);
         if constexpr (P) {
             if (A.traceback && !failed) {
@@ -1052,7 +1091,7 @@ __device__ __forceinline__ void align_queries(const TierArgs &A) {
         const uint32_t qid = sh.qid;
         __syncthreads();
         if (qid == 0xFFFFFFFFu) break;
-        align_one<P>(A, s, sh, qid);
+        align_one<P, true>(A, s, sh, qid);
     }
 }
 
@@ -1172,7 +1211,7 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
         A.out = S.results[rc] + slot;
         A.max_lag = S.max_lag;
         A.max_score = S.max_score;
-        align_one<P>(A, s, sh, 0);
+        align_one<P, false>(A, s, sh, 0);
         if (threadIdx.x == 0) {
             __threadfence_system();
             st_release_sys(S.done[rc] + slot, ticket + 1);
