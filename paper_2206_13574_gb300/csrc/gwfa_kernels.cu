@@ -560,14 +560,21 @@ __device__ __forceinline__ bool first_fresh(long long prev, long long cand) {
 // Offer value `cand` to lane `ln` of tile (slot, v, kb): GwfExpand's max-merge
 // into H~; the lane joins the next Q if its offset strictly improved.
 template <bool P>
-__device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, uint32_t v, int kb,
-                                      int ln, typename VT<P>::T cand, int par, uint32_t *qcount, bool traceback) {
-    const typename VT<P>::T prev = atomicMax(&s.slots[slot].vals[ln], cand);
+__device__ __forceinline__ void offer_done(const Slab<P> &s, Sh &sh, uint32_t slot, uint32_t v, int kb,
+                                           int ln, typename VT<P>::T cand, typename VT<P>::T prev, int par,
+                                           uint32_t *qcount, bool traceback) {
     if (prev < 0) atomicAdd(&sh.visited, 1ull);
     if constexpr (P) {
         if (traceback && first_fresh(prev, cand)) __stcg(&s.slots[slot].trace[ln], 0u);
     }
     if (pj(prev) < pj(cand)) reg_append(&s.slots[slot].reg[par], s.qlist, qcount, s.cap, slot, v, kb, 1u << ln, sh);
+}
+
+template <bool P>
+__device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, uint32_t v, int kb,
+                                      int ln, typename VT<P>::T cand, int par, uint32_t *qcount, bool traceback) {
+    const typename VT<P>::T prev = atomicMax(&s.slots[slot].vals[ln], cand);
+    offer_done<P>(s, sh, slot, v, kb, ln, cand, prev, par, qcount, traceback);
 }
 
 // GwfExpand (Alg. 3) over the extended frontier, with GwfPrune (Alg. 4) applied
@@ -644,11 +651,18 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
             nh[u] = tile_hash(nkey[u], s.mask);
             ncur[u] = out ? __ldcg(&s.slots[nh[u]].key) : 0ull;
         }
+        // a boundary lane whose early read found the neighbour tile merges into it
+        // together with this tile's merges
+        bool near[U];
+        T nprev[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             prev[u] = (T)0x7FFFFFFF;
             if (valid[u] && cand[u] >= 0)
                 prev[u] = atomicMax(&s.slots[h[u].slot_mask & 0xFFFFFFu].vals[ln], cand[u]);
+            near[u] = ncur[u] == nkey[u] && valid[u] && ((ln == 7 && ins[u]) || (ln == 0 && del[u]));
+            nprev[u] = 0;
+            if (near[u]) nprev[u] = atomicMax(&s.slots[nh[u]].vals[7 - ln], ln == 7 ? c_ins[u] : c_del[u]);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -666,12 +680,20 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (valid[u] && ln == 7 && ins[u]) {   // insertion leaves the tile: (v, 8(kb+1))
-                const int t = find_or_insert_at(s, sh, nkey[u], nh[u], ncur[u]);
-                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb + 1, 0, c_ins[u], par, qcount, traceback);
+                if (near[u]) {
+                    offer_done<P>(s, sh, nh[u], h[u].v, h[u].kb + 1, 0, c_ins[u], nprev[u], par, qcount, traceback);
+                } else {
+                    const int t = find_or_insert_at(s, sh, nkey[u], nh[u], ncur[u]);
+                    if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb + 1, 0, c_ins[u], par, qcount, traceback);
+                }
             }
             if (valid[u] && ln == 0 && del[u]) {   // deletion leaves the tile: (v, 8 kb - 1)
-                const int t = find_or_insert_at(s, sh, nkey[u], nh[u], ncur[u]);
-                if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb - 1, 7, c_del[u], par, qcount, traceback);
+                if (near[u]) {
+                    offer_done<P>(s, sh, nh[u], h[u].v, h[u].kb - 1, 7, c_del[u], nprev[u], par, qcount, traceback);
+                } else {
+                    const int t = find_or_insert_at(s, sh, nkey[u], nh[u], ncur[u]);
+                    if (t >= 0) offer<P>(s, sh, (uint32_t)t, h[u].v, h[u].kb - 1, 7, c_del[u], par, qcount, traceback);
+                }
             }
         }
     }
