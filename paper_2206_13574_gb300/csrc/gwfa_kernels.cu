@@ -46,10 +46,10 @@ namespace {
 constexpr long long kTagPend = 0, kTagFresh = 1, kTagSettled = 2;
 constexpr uint32_t kBaseMask = 0x3FFFFFFFu;
 constexpr int kStack = 6;   // depth-first spill stack per thread (exact mode)
-// Tiles an 8-lane group takes per iteration (exact mode; pruning mode expands one):
-// two, kept in flight together, when a phase has at least kWideTiles entries per
-// group, else one.
-constexpr int kWideTiles = 16;
+// Tiles an 8-lane group takes per claim (both phases).  With a warp's four groups
+// claiming together, one is fastest: two in flight hid more latency only while each
+// group claimed alone, and their registers spill.
+constexpr int kGroupTiles = 1;
 constexpr uint32_t kNoTrace = 0x3FFFFFFFu;   // trace index of the start diagonal (no predecessor)
 
 template <bool P> struct VT;
@@ -828,9 +828,7 @@ __device__ void evict_behind(const Slab<true> &s, Sh &sh, long long amax, int la
     __syncthreads();
 }
 
-// kWide: large phases may take two tiles per group (the batch kernels; the server
-// kernel, whose ring handling holds more registers, takes one).
-template <bool P, bool kWide>
+template <bool P>
 __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t qid) {
     const DevGraph &g = A.g;
     const uint64_t qo = A.q_off[qid];
@@ -963,12 +961,8 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                     resolve_spill_traces(g, s, sh, sh.nreq[round & 1]);
                 }
             } else {
-                if (kWide && n_list >= kWideTiles * (blockDim.x >> 3))
-                    extend_round_exact<2>(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
-                                          next_count, claim);
-                else
-                    extend_round_exact<1>(g, s, sh, q, list, n_list, phase & 1, next_phase & 1, next_list,
-                                          next_count, claim);
+                extend_round_exact<kGroupTiles>(g, s, sh, q, list, n_list, phase & 1, next_phase & 1,
+                                                next_list, next_count, claim);
             }
             // every exit decision comes from a barrier reduction: sh.err may be set by
             // threads that already run the next phase, so it is never re-read for control
@@ -1005,17 +999,8 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         }
         uint32_t *claim = &sh.claim[cstep % 3];
         ++cstep;
-        if constexpr (!P) {
-            if (kWide && sh.ne >= kWideTiles * (blockDim.x >> 3))
-                expand_all<P, 2>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
-                                 A.traceback != 0);
-            else
-                expand_all<P, 1>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
-                                 A.traceback != 0);
-        } else {
-            expand_all<P, 1>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1], claim,
-                             A.traceback != 0);
-        }
+        expand_all<P, kGroupTiles>(s, sh, q, sh.ne, prune_on, amax, A.max_lag, phase & 1, &sh.nq[d & 1],
+                                   claim, A.traceback != 0);
         failed = __syncthreads_or(sh.err != 0);
         if constexpr (P) {
             if (A.traceback && !failed) {
@@ -1113,7 +1098,7 @@ __device__ __forceinline__ void align_queries(const TierArgs &A) {
         const uint32_t qid = sh.qid;
         __syncthreads();
         if (qid == 0xFFFFFFFFu) break;
-        align_one<P, true>(A, s, sh, qid);
+        align_one<P>(A, s, sh, qid);
     }
 }
 
@@ -1233,7 +1218,7 @@ __global__ void __launch_bounds__(512, 4) server_kernel(ServerArgs S) {
         A.out = S.results[rc] + slot;
         A.max_lag = S.max_lag;
         A.max_score = S.max_score;
-        align_one<P, false>(A, s, sh, 0);
+        align_one<P>(A, s, sh, 0);
         if (threadIdx.x == 0) {
             __threadfence_system();
             st_release_sys(S.done[rc] + slot, ticket + 1);
