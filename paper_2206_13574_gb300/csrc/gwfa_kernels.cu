@@ -215,6 +215,31 @@ __device__ __forceinline__ int lcp_finish(const QCtx &q, int i, const uint32_t *
     return min(l, maxl);
 }
 
+// Pruning mode: atomics on slab memory (always device global memory) issued in the
+// global state space; the slab pointers come from shared memory, where the compiler
+// no longer knows their space.
+__device__ __forceinline__ uint32_t g_exch(uint32_t *p, uint32_t v) {
+    uint32_t r;
+    asm volatile("atom.global.exch.b32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+    return r;
+}
+__device__ __forceinline__ long long g_max(long long *p, long long v) {
+    long long r;
+    asm volatile("atom.global.max.s64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+    return r;
+}
+__device__ __forceinline__ unsigned long long g_cas(unsigned long long *p, unsigned long long c,
+                                                    unsigned long long v) {
+    unsigned long long r;
+    asm volatile("atom.global.cas.b64 %0, [%1], %2, %3;" : "=l"(r) : "l"(p), "l"(c), "l"(v) : "memory");
+    return r;
+}
+template <bool P, class T>
+__device__ __forceinline__ T slab_max(T *p, T v) {
+    if constexpr (P) return g_max(p, v);
+    else return atomicMax(p, v);
+}
+
 __device__ __forceinline__ unsigned long long tile_key(uint32_t v, int kb) {
     return ((unsigned long long)v << 32) | (uint32_t)kb;
 }
@@ -232,7 +257,9 @@ __device__ int find_or_insert_at(const Slab<P> &s, Sh &sh, unsigned long long ke
         if (probe > 0) cur = __ldcg(&s.slots[h].key);
         if (cur == key) return (int)h;
         if (cur == kEmptyKey) {
-            const unsigned long long prev = atomicCAS(&s.slots[h].key, kEmptyKey, key);
+            unsigned long long prev;
+            if constexpr (P) prev = g_cas(&s.slots[h].key, kEmptyKey, key);
+            else prev = atomicCAS(&s.slots[h].key, kEmptyKey, key);
             if (prev == kEmptyKey) {
                 const uint32_t t = atomicAdd(&sh.nt, 1u);
                 s.touched[t] = h;   // t < cap: each claim takes a distinct empty slot
@@ -448,7 +475,7 @@ __device__ void extend_round_prune(const DevGraph &g, const Slab<true> &s, Sh &s
         if (e >= n_list) continue;
         const LEnt ent = ld_lent(&list[e]);
         uint32_t m = 0, eidx = 0;
-        if (ln == 0) m = atomicExch(&s.slots[ent.slot].reg[par], 0u);
+        if (ln == 0) m = g_exch(&s.slots[ent.slot].reg[par], 0u);
         long long val = __ldcg(&s.slots[ent.slot].vals[ln]);
         const uint2 vi = __ldg((const uint2 *)&g.vinfo[ent.v]);   // label word, |v|
         const uint32_t tr = traceback ? __ldcg(&s.slots[ent.slot].trace[ln]) : 0u;
@@ -518,7 +545,7 @@ __device__ void apply_spill_requests(const DevGraph &g, const Slab<true> &s, Sh 
             const uint32_t u = __ldg(&g.arc_dst[a]);
             const int su = find_or_insert(s, sh, tile_key(u, ku >> 3));
             if (su < 0) return;
-            const long long prev = atomicMax(&s.slots[su].vals[ku & 7], cand);
+            const long long prev = g_max(&s.slots[su].vals[ku & 7], cand);
             if (prev < 0) {
                 atomicAdd(&sh.visited, 1ull);
                 atomicAdd(&sh.spills, 1ull);
@@ -573,7 +600,7 @@ __device__ __forceinline__ void offer_done(const Slab<P> &s, Sh &sh, uint32_t sl
 template <bool P>
 __device__ __forceinline__ void offer(const Slab<P> &s, Sh &sh, uint32_t slot, uint32_t v, int kb,
                                       int ln, typename VT<P>::T cand, int par, uint32_t *qcount, bool traceback) {
-    const typename VT<P>::T prev = atomicMax(&s.slots[slot].vals[ln], cand);
+    const typename VT<P>::T prev = slab_max<P>(&s.slots[slot].vals[ln], cand);
     offer_done<P>(s, sh, slot, v, kb, ln, cand, prev, par, qcount, traceback);
 }
 
@@ -659,10 +686,10 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
         for (int u = 0; u < U; ++u) {
             prev[u] = (T)0x7FFFFFFF;
             if (valid[u] && cand[u] >= 0)
-                prev[u] = atomicMax(&s.slots[h[u].slot_mask & 0xFFFFFFu].vals[ln], cand[u]);
+                prev[u] = slab_max<P>(&s.slots[h[u].slot_mask & 0xFFFFFFu].vals[ln], cand[u]);
             near[u] = ncur[u] == nkey[u] && valid[u] && ((ln == 7 && ins[u]) || (ln == 0 && del[u]));
             nprev[u] = 0;
-            if (near[u]) nprev[u] = atomicMax(&s.slots[nh[u]].vals[7 - ln], ln == 7 ? c_ins[u] : c_del[u]);
+            if (near[u]) nprev[u] = slab_max<P>(&s.slots[nh[u]].vals[7 - ln], ln == 7 ? c_ins[u] : c_del[u]);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
