@@ -325,7 +325,6 @@ __device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const
             if (su < 0) return;
             const int prev = atomicMax(&s.slots[su].vals[ku & 7], 0);
             if (prev < 0) {
-                atomicAdd(&sh.visited, 1ull);
                 atomicAdd(&sh.spills, 1ull);
                 if (top < kStack) {
                     st_slot[top] = (uint32_t)su;
@@ -590,8 +589,8 @@ template <bool P>
 __device__ __forceinline__ void offer_done(const Slab<P> &s, Sh &sh, uint32_t slot, uint32_t v, int kb,
                                            int ln, typename VT<P>::T cand, typename VT<P>::T prev, int par,
                                            uint32_t *qcount, bool traceback) {
-    if (prev < 0) atomicAdd(&sh.visited, 1ull);
     if constexpr (P) {
+        if (prev < 0) atomicAdd(&sh.visited, 1ull);
         if (traceback && first_fresh(prev, cand)) __stcg(&s.slots[slot].trace[ln], 0u);
     }
     if (pj(prev) < pj(cand)) reg_append(&s.slots[slot].reg[par], s.qlist, qcount, s.cap, slot, v, kb, 1u << ln, sh);
@@ -694,7 +693,9 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (!(valid[u] && cand[u] >= 0)) continue;
-            if (prev[u] < 0) atomicAdd(&sh.visited, 1ull);
+            if constexpr (P) {
+                if (prev[u] < 0) atomicAdd(&sh.visited, 1ull);   // exact mode counts at query end
+            }
             if constexpr (P) {
                 if (traceback && first_fresh(prev[u], cand[u]))
                     __stcg(&s.slots[h[u].slot_mask & 0xFFFFFFu].trace[ln], 0u);
@@ -904,7 +905,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                 v0 = 0;
             }
             s.slots[slot].vals[0] = v0;
-            sh.visited = 1;
+            if constexpr (P) sh.visited = 1;
             reg_append(&s.slots[slot].reg[1], s.qlist, &sh.nq[0], s.cap, (uint32_t)slot, vs, 0, 1u, sh);
         }
     }
@@ -931,7 +932,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
                     s.slots[slot].vals[ln] = j;
                 }
             }
-            atomicAdd(&sh.visited, (unsigned long long)__popc(bits));
+            if constexpr (P) atomicAdd(&sh.visited, (unsigned long long)__popc(bits));
             reg_append(&s.slots[slot].reg[1], s.qlist, &sh.nq[0], s.cap, (uint32_t)slot, vs, kb, bits, sh);
         }
         __syncthreads();
@@ -1058,6 +1059,17 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
     __syncthreads();
     if (failed) status = sh.err;   // stable now: every thread has left the processing phases
     const uint32_t nt = sh.nt;
+    if constexpr (!P) {
+        // exact mode never removes a diagonal from H~, so the visited count is the
+        // number of lanes of the touched tiles that hold an offset
+        const uint32_t ntc = min(nt, s.cap);
+        uint32_t c = 0;
+        for (uint32_t t = threadIdx.x; t < ntc * kTile; t += blockDim.x)
+            c += __ldcg(&s.slots[__ldcg(&s.touched[t / kTile])].vals[t % kTile]) >= 0 ? 1u : 0u;
+        c = __reduce_add_sync(0xFFFFFFFFu, c);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&sh.visited, (unsigned long long)c);
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         if (status == GWFA_ERR_CAPACITY && A.retry) {
             const uint32_t r = atomicAdd(A.retry_count, 1u);
