@@ -105,6 +105,9 @@ struct Sh {
     uint32_t ne;        // extended-frontier entries this score
     uint32_t nt;        // tiles claimed (touched) this query
     uint32_t score_cells;
+    // 32-bit shares of the 64-bit totals, folded in by thread 0 with an exchange
+    // (a 64-bit shared-memory atomic costs far more than a 32-bit one)
+    uint32_t spills32, visited32, pruned32;
     unsigned long long amax;
     unsigned long long cells, visited, pruned, spills, evicted;
     uint32_t nsurv;     // memory bound: tiles kept by the last eviction
@@ -325,7 +328,7 @@ __device__ void spill_dfs(const DevGraph &g, const Slab<false> &s, Sh &sh, const
             if (su < 0) return;
             const int prev = atomicMax(&s.slots[su].vals[ku & 7], 0);
             if (prev < 0) {
-                atomicAdd(&sh.spills, 1ull);
+                atomicAdd(&sh.spills32, 1u);
                 if (top < kStack) {
                     st_slot[top] = (uint32_t)su;
                     st_u[top] = u;
@@ -546,8 +549,8 @@ __device__ void apply_spill_requests(const DevGraph &g, const Slab<true> &s, Sh 
             if (su < 0) return;
             const long long prev = g_max(&s.slots[su].vals[ku & 7], cand);
             if (prev < 0) {
-                atomicAdd(&sh.visited, 1ull);
-                atomicAdd(&sh.spills, 1ull);
+                atomicAdd(&sh.visited32, 1u);
+                atomicAdd(&sh.spills32, 1u);
                 __stcg(&s.slots[su].trace[ku & 7], 0u);   // set by resolve_spill_traces
                 reg_append(&s.slots[su].reg[next_par], next_list, next_count, s.cap, (uint32_t)su, u, ku >> 3,
                            1u << (ku & 7), sh);
@@ -590,7 +593,7 @@ __device__ __forceinline__ void offer_done(const Slab<P> &s, Sh &sh, uint32_t sl
                                            int ln, typename VT<P>::T cand, typename VT<P>::T prev, int par,
                                            uint32_t *qcount, bool traceback) {
     if constexpr (P) {
-        if (prev < 0) atomicAdd(&sh.visited, 1ull);
+        if (prev < 0) atomicAdd(&sh.visited32, 1u);
         if (traceback && first_fresh(prev, cand)) __stcg(&s.slots[slot].trace[ln], 0u);
     }
     if (pj(prev) < pj(cand)) reg_append(&s.slots[slot].reg[par], s.qlist, qcount, s.cap, slot, v, kb, 1u << ln, sh);
@@ -642,7 +645,7 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
                 const long long a = (long long)i + (long long)b + j;
                 if (amax - a >= (long long)max_lag) {
                     act = false;
-                    atomicAdd(&sh.pruned, 1ull);
+                    atomicAdd(&sh.pruned32, 1u);
                 }
             }
             ins[u] = act && i < q.n;                 // (k+1, j)
@@ -694,7 +697,7 @@ __device__ void expand_all(const Slab<P> &s, Sh &sh, const QCtx &q, uint32_t n_e
         for (int u = 0; u < U; ++u) {
             if (!(valid[u] && cand[u] >= 0)) continue;
             if constexpr (P) {
-                if (prev[u] < 0) atomicAdd(&sh.visited, 1ull);   // exact mode counts at query end
+                if (prev[u] < 0) atomicAdd(&sh.visited32, 1u);   // exact mode counts at query end
             }
             if constexpr (P) {
                 if (traceback && first_fresh(prev[u], cand[u]))
@@ -890,6 +893,7 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         sh.err = 0;
         sh.nt = 0;
         sh.cells = sh.visited = sh.pruned = sh.spills = sh.evicted = 0;
+        sh.spills32 = sh.visited32 = sh.pruned32 = 0;
         sh.peak = 0;
         sh.nq[0] = sh.nq[1] = 0;
         sh.claim[0] = sh.claim[1] = sh.claim[2] = 0;
@@ -1003,6 +1007,9 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
         }
         if (threadIdx.x == 0) {
             sh.cells += sh.score_cells;
+            sh.spills += atomicExch(&sh.spills32, 0u);
+            sh.visited += atomicExch(&sh.visited32, 0u);
+            sh.pruned += atomicExch(&sh.pruned32, 0u);
             sh.peak = max(sh.peak, sh.score_cells);
         }
         if (A.stats && threadIdx.x == 0) {
@@ -1078,13 +1085,13 @@ __device__ void align_one(const TierArgs &A, const Slab<P> &s, Sh &sh, uint32_t 
             gwfa_result r = {};
             r.status = status;
             r.edit_distance = status == 0 ? d : -1;
-            r.is_upper_bound = sh.pruned > 0 ? 1 : 0;
+            r.is_upper_bound = sh.pruned + sh.pruned32 > 0 ? 1 : 0;
             r.n_scores = (uint32_t)(d + 1);
             r.cells = sh.cells;
-            r.visited = sh.visited;
+            r.visited = sh.visited + sh.visited32;
             r.peak_frontier = sh.peak;
-            r.pruned = sh.pruned;
-            r.spills = sh.spills;
+            r.pruned = sh.pruned + sh.pruned32;
+            r.spills = sh.spills + sh.spills32;
             r.evicted = sh.evicted;
             if constexpr (P) {
                 if (A.traceback && status == 0) {
